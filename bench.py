@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of the CountGauss transform T.X = G.(S.X) on GB300.
+
+One step = one cg_apply_csr call on the large NMF-like workload (n = 2^24 rows,
+d = 64, Bernoulli density 0.05, U[0,1) values, m = 32, B = 2^17, seed 2): the
+CountSketch scatter, the in-kernel Gaussian contraction and its split-K sum.
+Inputs are resident in HBM when the timed region starts; the CSR arrays (~500 MB)
+exceed L2, so no flush is needed between steps.
+
+Printed JSON line (rank 0):
+  value          nnz(X)/s over all ranks (weak scaling: every rank sketches its own
+                 shard of n rows, global row offset rank*n; the m x d outputs are
+                 summed across ranks each step)
+  roofline       the scatter kernel (dominant): algorithmic bytes per launch
+                 (8 nnz + 4 (n+1) + 4 B d) over its CUDA-event duration, against the
+                 measured HBM copy bandwidth
+  plain          the plain G~.X on the same input and GPU, and the speedup over it
+  e2e            the same metric with the CSR copied host->device and Y read back
+                 every step, through the same public call
+  cpu_baseline   the FP64 oracle on this machine's host cores (rank 0, N = 1)
+
+--impl reference times that oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "nmf_n16M_d64"
+METRIC = "CountGauss nnz(X)/s & HBM-roofline %; speedup vs plain G̃·X, same GB300"
+UNIT = "nnz/s"
+
+# dram bytes (read + write) per launch of the scatter kernel from one ncu capture,
+# keyed by the sha256 of the kernel source it was taken on (null once it changes)
+NCU_TRAFFIC = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [ln.strip().split(",") for ln in f if ln.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1606_05732_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ------------------------------------------------------------------------------------
+def oracle_sample(workload: str, fraction: float):
+    from paper_1606_05732_gb300 import synth
+    X, w = synth.workload_csr(workload, scale_rows=fraction)
+    return X, w
+
+
+def time_oracle(X, w, steps: int, warmup: int):
+    import oracle
+    oracle.build()
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        oracle.apply_csr(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals)
+        dt = time.perf_counter() - t0
+        if it >= warmup:
+            times.append(dt)
+    return times
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    fraction = 0.25
+    X, w = oracle_sample(args.workload, fraction)
+    times = time_oracle(X, w, args.steps, args.warmup)
+    step = statistics.mean(times)
+    value = X.nnz / step
+    sample = (f"{fraction:.2f} of the rows of {args.workload} (n={X.n}, nnz={X.nnz}, m={w['m']}, B={w['B']}): "
+              f"one full oracle apply per step, single thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": X.n, "d": X.d, "nnz": X.nnz, "m": w["m"], "B": w["B"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1606_05732_gb300 import _lib, countgauss, synth
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    wl = dict(synth.WORKLOADS[args.workload])
+    n, d, m, B, seed = wl["n"], wl["d"], wl["m"], wl["B"], wl["seed"]
+    X = synth.csr_bernoulli(n, d, wl["p"], seed=seed + 7919 * rank, values=wl["values"])
+    nnz = X.nnz
+    rp_h = torch.from_numpy(X.row_ptr.astype(np.int32)).pin_memory()
+    ci_h = torch.from_numpy(X.col_idx).pin_memory()
+    v_h = torch.from_numpy(X.vals).pin_memory()
+    rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
+    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n)
+    Y = torch.empty(m, d, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.apply_csr(rp, ci, v, out=Y)
+        if pg is not None:
+            pg.all_reduce(Y)
+
+    for _ in range(args.warmup):
+        step()
+    plan.check()
+    plan.enable_timing(True)
+    plan.kernel_time(_lib.KERNEL_SKETCH)
+    plan.kernel_time(_lib.KERNEL_CONTRACT)
+
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    ms_total = e0.elapsed_time(e1)
+    sketch_ms, sketch_n = plan.kernel_time(_lib.KERNEL_SKETCH)
+    contract_ms, contract_n = plan.kernel_time(_lib.KERNEL_CONTRACT)
+    plan.enable_timing(False)
+    plan.check()
+    if pg is not None:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * nnz / (ms_step / 1e3)
+
+    # roofline of the scatter kernel
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 8 * nnz + 4 * (n + 1) + 4 * B * d
+    sketch_avg_s = (sketch_ms / max(1, sketch_n)) / 1e3
+    achieved = alg_bytes / sketch_avg_s / 1e9
+    src = source_hash("cg_sketch.cu", "cg_rng.cuh")
+    traffic = NCU_TRAFFIC.get(src)
+
+    # plain G~.X on the same input
+    plain_steps = max(3, args.steps // 4)
+    Yp = torch.empty_like(Y)
+    for _ in range(2):
+        plan.plain_csr(rp, ci, v, out=Yp)
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(plain_steps):
+        plan.plain_csr(rp, ci, v, out=Yp)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = p0.elapsed_time(p1) / plain_steps
+
+    # end to end through the same call: H2D of the CSR, apply, D2H of Y, every step
+    rp2, ci2, v2 = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(v)
+    Y_h = torch.empty(m, d, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        rp2.copy_(rp_h, non_blocking=True)
+        ci2.copy_(ci_h, non_blocking=True)
+        v2.copy_(v_h, non_blocking=True)
+        plan.apply_csr(rp2, ci2, v2, out=Y)
+        if pg is not None:
+            pg.all_reduce(Y)
+        Y_h.copy_(Y, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(3, args.steps // 2)
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    q1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = q0.elapsed_time(q1) / e2e_steps
+    if pg is not None:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = int(rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 4)
+    d2h = int(m * d * 4)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the full workload once (n={n}, nnz={nnz}), FP64, single thread, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "p": wl["p"], "values": wl["values"],
+                       "nnz_per_rank": nnz, "m": m, "B": B, "seed": seed,
+                       "l2": "CSR inputs (%.0f MB) exceed L2; no flush" % (h2d / 1e6)},
+            "roofline": {"kernel": "sketch_csr_atomic_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sketch_avg_s * 1e3,
+                         "launches": sketch_n},
+            "stages_ms": {"sketch_kernel": sketch_ms / max(1, sketch_n),
+                          "contract_kernel": contract_ms / max(1, contract_n)},
+            "plain": {"ms_per_step": plain_ms, "value": world * nnz / (plain_ms / 1e3), "unit": UNIT,
+                      "speedup_countgauss_over_plain": plain_ms / ms_step},
+            "e2e": {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * countgauss.h -- C ABI of libcountgauss, a GB300 (sm_103a) implementation of the
+ * CountGauss transform of Kapralov, Potluru and Woodruff, "How to Fake Multiply by
+ * a Gaussian Matrix".
+ *
+ * The transform (Section 1.1 "Our Results"; Section 2, Theorem 1):
+ *   X  is n x d (n >> d), sparse (CSR) or dense;
+ *   S  is a B x n CountSketch: column i of S has one nonzero, sigma(i) = +-1, at row
+ *      h(i) in [0, B)  (Section 1.1; Section 7);
+ *   G  is m x B with i.i.d. N(0,1) entries (Theorem 1: unit variance, no scaling);
+ *   T = G.S, and T.X is computed as G.(S.X) in O(nnz(X)) + O(m.B.d) work instead
+ *   of the O(nnz(X).m) of the plain product G~.X with an m x n Gaussian G~
+ *   (Abstract; Section 4; Algorithm 1 steps 1-2).
+ *
+ * Randomness.  h, sigma, G and G~ are pure functions of (seed, index): Philox4x32-10
+ * (Salmon et al., SC'11) with key (lo32(seed), hi32(seed)) and counter
+ * (lo32(idx), hi32(idx), tag, 0).  tag 0, idx = global row i: h(i) = floor(w0.B/2^32),
+ * sigma(i) = -1 iff bit 31 of w1 is set.  Uniforms u(w) = (2(w>>9)+1).2^-24.  Entry
+ * (r, c) of an R x C Gaussian with tag t is lane r%4 of the Box-Muller quadruple
+ *   (sqrt(-2 ln u0) cos 2pi u1, sqrt(-2 ln u0) sin 2pi u1,
+ *    sqrt(-2 ln u2) cos 2pi u3, sqrt(-2 ln u2) sin 2pi u3)
+ * of the call at idx = c.ceil(R/4) + floor(r/4): G is tag 1 (R = m, C = B), G~ is
+ * tag 2 (R = m, C = global row).  Because nothing is stored, every process that
+ * shares the seed holds the same T (the distributed remark of Section 4); a shard of
+ * X whose first row is global row o sets CG_OPT_ROW_OFFSET = o, and the shards'
+ * outputs sum to the output of the whole X.
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer argument named as device memory must be device memory of the
+ *     current CUDA device; the caller owns it, allocates it and frees it.  The plan
+ *     owns host memory only.
+ *   - Dense matrices are row-major fp32.  Y is m x d, SX is B x d, W is B x d.
+ *   - CSR X: row_ptr int32[n+1] with row_ptr[0] = 0 and row_ptr[n] = nnz,
+ *     col_idx int32[nnz] in [0, d) (any order within a row; duplicates are summed),
+ *     vals fp32[nnz].  nnz < 2^31.
+ *   - ws is a device workspace of at least cg_workspace_size() bytes, 256-byte
+ *     aligned.  Its first 256 bytes hold a device status word that the kernels set
+ *     when a bounds check fails (the offending element is skipped, never accessed)
+ *     or a bounded wait gives up; cg_plan_check() reads and clears it.  The caller
+ *     zeroes those 256 bytes once when it allocates the workspace; kernels only
+ *     ever set bits, so a nonzero word means some call since the last check failed.
+ *   - Entry points are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream), never synchronise, never print and never abort.  Argument
+ *     errors are found on the host before anything is launched and reported as
+ *     CG_ERR_INVALID_ARG / CG_ERR_UNSUPPORTED / CG_ERR_WORKSPACE; a launch failure
+ *     is CG_ERR_CUDA.
+ *   - A plan may be used from one host thread at a time.
+ */
+#ifndef COUNTGAUSS_H
+#define COUNTGAUSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CG_API __attribute__((visibility("default")))
+#else
+#define CG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cg_plan cg_plan;
+
+typedef enum cg_status {
+    CG_OK = 0,
+    CG_ERR_INVALID_ARG = 1,   /* bad size, null pointer, misaligned buffer */
+    CG_ERR_UNSUPPORTED = 2,   /* valid request outside what this build implements */
+    CG_ERR_WORKSPACE = 3,     /* ws_bytes smaller than cg_workspace_size() */
+    CG_ERR_CUDA = 4,          /* a CUDA call or kernel launch failed */
+    CG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (batched path) */
+    CG_ERR_DEVICE_BOUNDS = 6, /* a kernel met an index outside its buffer and skipped it */
+    CG_ERR_NO_DEVICE = 7      /* no usable CUDA device */
+} cg_status;
+
+typedef enum cg_precision {
+    CG_PREC_FP32 = 0,     /* FFMA, fp32 throughout */
+    CG_PREC_BF16 = 1,     /* tcgen05 kind::f16, bf16 G and SX, fp32 accumulate in TMEM */
+    CG_PREC_BF16X3 = 2,   /* split bf16: hi.hi + hi.lo + lo.hi, fp32 accumulate */
+    CG_PREC_FP8_E4M3 = 3  /* tcgen05 kind::f8f6f4, e4m3 with per-tile scales */
+} cg_precision;
+
+typedef enum cg_option {
+    CG_OPT_PRECISION = 1,     /* cg_precision of the Gaussian contraction (default FP32) */
+    CG_OPT_DETERMINISTIC = 2, /* 0: atomic scatter (default); 1: sort-by-bucket scatter,
+                                 bit-reproducible run to run */
+    CG_OPT_ROW_OFFSET = 3,    /* global index of local row 0 (default 0) */
+    CG_OPT_KSPLIT = 4,        /* CTAs along B in the contraction; 0 = automatic */
+    CG_OPT_SKETCH_CTAS = 5,   /* CTAs of the scatter kernel; 0 = automatic */
+    CG_OPT_TIMING = 6         /* 1: record CUDA events around each main kernel launch
+                                 (read with cg_plan_timing); 0 (default): off */
+} cg_option;
+
+typedef enum cg_kernel {
+    CG_KERNEL_SKETCH = 0,     /* the CSR / dense scatter kernel (not the SX memset) */
+    CG_KERNEL_CONTRACT = 1,   /* the Gaussian contraction kernel (not the split-K sum) */
+    CG_KERNEL_PLAIN = 2,      /* the plain G~.X kernel (not the split sum) */
+    CG_KERNEL_ADJOINT_W = 3,  /* W = G^T.dY */
+    CG_KERNEL_GATHER = 4,     /* dX = S^T.W */
+    CG_KERNEL_COUNT = 5
+} cg_kernel;
+
+typedef enum cg_op {
+    CG_OP_APPLY_CSR = 0,
+    CG_OP_APPLY_DENSE = 1,
+    CG_OP_ADJOINT_DENSE = 2,
+    CG_OP_ADJOINT_CSR = 3,
+    CG_OP_PLAIN_CSR = 4,
+    CG_OP_SKETCH = 5,         /* cg_sketch_csr / cg_sketch_dense alone */
+    CG_OP_CONTRACT = 6        /* cg_contract alone */
+} cg_op;
+
+/* ---- plans ---------------------------------------------------------------- */
+
+/* Create a plan for T = G.S with X of n rows and d columns, m output rows, B sketch
+ * rows and the given seed (Section 1.1; Theorem 1).  Limits: 0 <= n < 2^31 - 1,
+ * 1 <= d <= 65536, 1 <= m <= 65536, 1 <= B < 2^31, B.d < 2^40.  No CUDA call is made.
+ * *out receives a host-side handle to free with cg_plan_destroy. */
+CG_API cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t seed, cg_plan **out);
+
+CG_API cg_status cg_plan_destroy(cg_plan *plan);
+
+/* Set one cg_option.  Values outside the option's range give CG_ERR_INVALID_ARG. */
+CG_API cg_status cg_plan_set_option(cg_plan *plan, int32_t option, int64_t value);
+CG_API cg_status cg_plan_get_option(const cg_plan *plan, int32_t option, int64_t *value);
+
+/* Device workspace, in bytes, that `op` needs for a call with `nnz` stored entries
+ * (ignored for dense ops).  Depends on the plan's options and on the current
+ * device's SM count; query it after setting options. */
+CG_API cg_status cg_workspace_size(const cg_plan *plan, int32_t op, int64_t nnz, size_t *bytes);
+
+/* Synchronise `stream`, read the device status word in ws and clear it.  Returns
+ * CG_OK, CG_ERR_DEVICE_BOUNDS or CG_ERR_TIMEOUT (or CG_ERR_CUDA). */
+CG_API cg_status cg_plan_check(const cg_plan *plan, void *ws, void *stream);
+
+CG_API const char *cg_status_string(cg_status status);
+
+/* With CG_OPT_TIMING on, every launch of `kernel` made through this plan is
+ * bracketed by a pair of CUDA events on the launching stream.  This call waits for
+ * the recorded events, returns the summed elapsed time (ms) and the number of
+ * launches since the last call, and forgets them. */
+CG_API cg_status cg_plan_timing(cg_plan *plan, int32_t kernel, double *total_ms, int64_t *launches);
+
+/* ---- the transform -------------------------------------------------------- */
+
+/* Y = G.(S.X) for CSR X (Section 1.1; Algorithm 1 steps 1-2).  Stage 1 scatters
+ * sigma(i).X[i,:] into row h(i) of SX (B x d, in ws); stage 2 contracts SX with G,
+ * generated in-kernel, never stored.  Y (device, m x d) is overwritten. */
+CG_API cg_status cg_apply_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
+                       const float *vals, int64_t nnz, float *Y,
+                       void *ws, size_t ws_bytes, void *stream);
+
+/* Y = G.(S.X) for dense X (device, n x d, row stride ldx >= d floats). */
+CG_API cg_status cg_apply_dense(cg_plan *plan, const float *X, int64_t ldx, float *Y,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Adjoint: dX = S^T.(G^T.dY) (T is linear, Section 1.1).  dY is m x d (device).
+ * row_ptr == NULL: dX is dense n x d (device).  Otherwise dX holds nnz values, the
+ * gradient read at the stored entries of the CSR pattern (row_ptr, col_idx).
+ * G is regenerated from the seed, W = G^T.dY (B x d) lives in ws. */
+CG_API cg_status cg_apply_adjoint(cg_plan *plan, const float *dY, const int32_t *row_ptr,
+                           const int32_t *col_idx, int64_t nnz, float *dX,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/* The plain product Y = G~.X that the method replaces (Abstract; Section 4), with
+ * the m x n Gaussian G~ generated on the fly, one column per non-empty row of X.
+ * Y (device, m x d) is overwritten. */
+CG_API cg_status cg_plain_gaussian_apply(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
+                                  const float *vals, int64_t nnz, float *Y,
+                                  void *ws, size_t ws_bytes, void *stream);
+
+/* ---- stages (for stage-wise checks and measurement) ----------------------- */
+
+/* SX = S.X alone (Section 1.1: O(nnz(X)) scatter).  SX (device, B x d) is
+ * overwritten.  Honours CG_OPT_DETERMINISTIC. */
+CG_API cg_status cg_sketch_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
+                        const float *vals, int64_t nnz, float *SX,
+                        void *ws, size_t ws_bytes, void *stream);
+
+CG_API cg_status cg_sketch_dense(cg_plan *plan, const float *X, int64_t ldx, float *SX,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* Y = G.SX alone (SX device, B x d).  Honours CG_OPT_PRECISION. */
+CG_API cg_status cg_contract(cg_plan *plan, const float *SX, float *Y,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* ---- the generator, exposed for bit-exact checks ---------------------------- */
+
+/* words[4t..4t+3] = Philox4x32-10 words of (seed, tag, idx0 + t), t < count
+ * (device uint32 buffer of 4.count). */
+CG_API cg_status cg_generate_words(uint64_t seed, uint32_t tag, uint64_t idx0, int64_t count,
+                            uint32_t *words, void *stream);
+
+/* h[t], sigma[t] of global rows row0 + t, t < count (device buffers). */
+CG_API cg_status cg_generate_hash_sign(uint64_t seed, int64_t B, int64_t row0, int64_t count,
+                                int32_t *h, int32_t *sigma, void *stream);
+
+/* Rows [r0, r1) x columns [c0, c1) of the R x C Gaussian with `tag` (1: G, 2: G~),
+ * row-major into out (device, (r1-r0) x (c1-c0) floats), with the same fp32
+ * Box-Muller the kernels use. */
+CG_API cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r0, int64_t r1,
+                               int64_t c0, int64_t c1, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COUNTGAUSS_H */

@@ -1,0 +1,250 @@
+"""Python binding of libcountgauss: torch tensors in, torch tensors out.
+
+PyTorch provides device memory and the current stream; every step of the transform
+runs in the library's CUDA kernels, reached through the C ABI of
+``include/countgauss.h``.  The functions here only check dtypes/devices, allocate
+outputs and workspaces with torch, and pass pointers.
+
+    plan = CountGauss(n, d, m, B, seed)
+    Y = plan.apply_csr(row_ptr, col_idx, vals)   # G.(S.X), m x d   (Section 1.1)
+    Y = plan.apply_dense(X)
+    dX = plan.adjoint(dY)                        # S^T G^T dY
+    Yp = plan.plain_csr(row_ptr, col_idx, vals)  # G~.X, the product it replaces
+    Y = countgauss_dense(X, plan)                # differentiable (autograd)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+_P = ctypes.c_void_p
+
+
+def _ptr(t) -> _P:
+    return _P(0) if t is None else _P(t.data_ptr())
+
+
+def _stream(device) -> _P:
+    return _P(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class CountGauss:
+    """A CountGauss plan T = G.S for X of n rows and d columns (cg_plan_create)."""
+
+    def __init__(self, n: int, d: int, m: int, B: int, seed: int, *, precision: str = "fp32",
+                 deterministic: bool = False, row_offset: int = 0, ksplit: int = 0, sketch_ctas: int = 0):
+        lib = _lib.load()
+        h = _P()
+        _lib.check("cg_plan_create", lib.cg_plan_create(n, d, m, B, seed, ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.n, self.d, self.m, self.B, self.seed = int(n), int(d), int(m), int(B), int(seed)
+        self._ws: dict = {}
+        self.set_option(_lib.OPT_PRECISION, _lib.PREC[precision])
+        self.set_option(_lib.OPT_DETERMINISTIC, int(bool(deterministic)))
+        self.set_option(_lib.OPT_ROW_OFFSET, int(row_offset))
+        self.set_option(_lib.OPT_KSPLIT, int(ksplit))
+        self.set_option(_lib.OPT_SKETCH_CTAS, int(sketch_ctas))
+        self.precision = precision
+        self.deterministic = bool(deterministic)
+        self.row_offset = int(row_offset)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.cg_plan_destroy(h)
+            self._h = None
+
+    # -- options and workspace ------------------------------------------------
+    def set_option(self, option: int, value: int) -> None:
+        _lib.check("cg_plan_set_option", self._lib.cg_plan_set_option(self._h, option, int(value)))
+        self._ws.clear()
+
+    def workspace_size(self, op: int, nnz: int = 0) -> int:
+        sz = ctypes.c_size_t()
+        _lib.check("cg_workspace_size", self._lib.cg_workspace_size(self._h, op, int(nnz), ctypes.byref(sz)))
+        return int(sz.value)
+
+    def workspace(self, op: int, nnz: int, device: torch.device) -> torch.Tensor:
+        need = self.workspace_size(op, nnz)
+        key = (device.index if device.index is not None else torch.cuda.current_device())
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+            ws[:256].zero_()  # status word starts clear
+            self._ws[key] = ws
+        return ws
+
+    def enable_timing(self, on: bool = True) -> None:
+        """Record CUDA events around each main kernel launch (CG_OPT_TIMING)."""
+        _lib.check("cg_plan_set_option", self._lib.cg_plan_set_option(self._h, _lib.OPT_TIMING, int(bool(on))))
+
+    def kernel_time(self, kernel: int):
+        """(total ms, launches) of `kernel` since the last call (cg_plan_timing)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _lib.check("cg_plan_timing", self._lib.cg_plan_timing(self._h, kernel, ctypes.byref(ms), ctypes.byref(n)))
+        return float(ms.value), int(n.value)
+
+    def check(self) -> None:
+        """Synchronise and raise if any kernel since the last check set the status word."""
+        for dev, ws in self._ws.items():
+            _lib.check("cg_plan_check", self._lib.cg_plan_check(self._h, _ptr(ws), _stream(ws.device)))
+
+    # -- the transform --------------------------------------------------------
+    def apply_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
+        """Y = G.(S.X) for CSR X (Section 1.1; Algorithm 1 steps 1-2)."""
+        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        col_idx = _need(col_idx, torch.int32, "col_idx")
+        vals = _need(vals, torch.float32, "vals")
+        dev = row_ptr.device
+        nnz = col_idx.numel()
+        Y = torch.empty(self.m, self.d, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_APPLY_CSR, nnz, dev)
+        _lib.check("cg_apply_csr", self._lib.cg_apply_csr(
+            self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
+        return Y
+
+    def apply_dense(self, X, out=None) -> torch.Tensor:
+        """Y = G.(S.X) for dense row-major X (n x d)."""
+        X = _need(X, torch.float32, "X")
+        dev = X.device
+        Y = torch.empty(self.m, self.d, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_APPLY_DENSE, 0, dev)
+        _lib.check("cg_apply_dense", self._lib.cg_apply_dense(
+            self._h, _ptr(X), X.shape[1] if X.dim() == 2 else self.d, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
+        return Y
+
+    def adjoint(self, dY, row_ptr=None, col_idx=None, out=None) -> torch.Tensor:
+        """dX = S^T.(G^T.dY): dense n x d, or nnz values at a CSR pattern."""
+        dY = _need(dY, torch.float32, "dY")
+        dev = dY.device
+        if row_ptr is None:
+            dX = torch.empty(self.n, self.d, dtype=torch.float32, device=dev) if out is None else out
+            nnz, op = 0, _lib.OP_ADJOINT_DENSE
+        else:
+            row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+            col_idx = _need(col_idx, torch.int32, "col_idx")
+            nnz, op = col_idx.numel(), _lib.OP_ADJOINT_CSR
+            dX = torch.empty(nnz, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(op, nnz, dev)
+        _lib.check("cg_apply_adjoint", self._lib.cg_apply_adjoint(
+            self._h, _ptr(dY), _ptr(row_ptr), _ptr(col_idx), nnz, _ptr(dX), _ptr(ws), ws.numel(), _stream(dev)))
+        return dX
+
+    def plain_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
+        """Y = G~.X with an on-the-fly m x n Gaussian (the product CountGauss replaces)."""
+        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        col_idx = _need(col_idx, torch.int32, "col_idx")
+        vals = _need(vals, torch.float32, "vals")
+        dev = row_ptr.device
+        nnz = col_idx.numel()
+        Y = torch.empty(self.m, self.d, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_PLAIN_CSR, nnz, dev)
+        _lib.check("cg_plain_gaussian_apply", self._lib.cg_plain_gaussian_apply(
+            self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
+        return Y
+
+    # -- stages -----------------------------------------------------------------
+    def sketch_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
+        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        col_idx = _need(col_idx, torch.int32, "col_idx")
+        vals = _need(vals, torch.float32, "vals")
+        dev = row_ptr.device
+        nnz = col_idx.numel()
+        SX = torch.empty(self.B, self.d, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_SKETCH, nnz, dev)
+        _lib.check("cg_sketch_csr", self._lib.cg_sketch_csr(
+            self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(SX), _ptr(ws), ws.numel(), _stream(dev)))
+        return SX
+
+    def sketch_dense(self, X, out=None) -> torch.Tensor:
+        X = _need(X, torch.float32, "X")
+        dev = X.device
+        SX = torch.empty(self.B, self.d, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_SKETCH, 0, dev)
+        _lib.check("cg_sketch_dense", self._lib.cg_sketch_dense(
+            self._h, _ptr(X), X.shape[1], _ptr(SX), _ptr(ws), ws.numel(), _stream(dev)))
+        return SX
+
+    def contract(self, SX, out=None) -> torch.Tensor:
+        SX = _need(SX, torch.float32, "SX")
+        dev = SX.device
+        Y = torch.empty(self.m, self.d, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_CONTRACT, 0, dev)
+        _lib.check("cg_contract", self._lib.cg_contract(
+            self._h, _ptr(SX), _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
+        return Y
+
+
+# -- generator dumps (bit-exact checks against the oracle) -----------------------
+def generate_words(seed: int, tag: int, idx0: int, count: int, device="cuda") -> torch.Tensor:
+    out = torch.empty(count, 4, dtype=torch.int32, device=device)
+    _lib.call("cg_generate_words", seed, tag, idx0, count, _ptr(out), _stream(out.device))
+    return out
+
+
+def generate_hash_sign(seed: int, B: int, row0: int, count: int, device="cuda"):
+    h = torch.empty(count, dtype=torch.int32, device=device)
+    s = torch.empty(count, dtype=torch.int32, device=device)
+    _lib.call("cg_generate_hash_sign", seed, B, row0, count, _ptr(h), _ptr(s), _stream(h.device))
+    return h, s
+
+
+def generate_gaussian(seed: int, tag: int, R: int, r0: int, r1: int, c0: int, c1: int, device="cuda"):
+    out = torch.empty(r1 - r0, c1 - c0, dtype=torch.float32, device=device)
+    _lib.call("cg_generate_gaussian", seed, tag, R, r0, r1, c0, c1, _ptr(out), _stream(out.device))
+    return out
+
+
+# -- autograd ---------------------------------------------------------------------
+class CountGaussDenseFn(torch.autograd.Function):
+    """Y = T.X for dense X; backward dX = T^T dY = S^T (G^T dY) with G regenerated."""
+
+    @staticmethod
+    def forward(ctx, X, plan):
+        ctx.plan = plan
+        return plan.apply_dense(X.contiguous())
+
+    @staticmethod
+    def backward(ctx, dY):
+        return ctx.plan.adjoint(dY.contiguous()), None
+
+
+class CountGaussCsrFn(torch.autograd.Function):
+    """Y = T.X for CSR X as a function of its stored values; backward is the
+    gradient at the stored entries only."""
+
+    @staticmethod
+    def forward(ctx, vals, row_ptr, col_idx, plan):
+        ctx.plan = plan
+        ctx.save_for_backward(row_ptr, col_idx)
+        return plan.apply_csr(row_ptr, col_idx, vals.contiguous())
+
+    @staticmethod
+    def backward(ctx, dY):
+        row_ptr, col_idx = ctx.saved_tensors
+        return ctx.plan.adjoint(dY.contiguous(), row_ptr, col_idx), None, None, None
+
+
+def countgauss_dense(X: torch.Tensor, plan: CountGauss) -> torch.Tensor:
+    return CountGaussDenseFn.apply(X, plan)
+
+
+def countgauss_csr(vals: torch.Tensor, row_ptr: torch.Tensor, col_idx: torch.Tensor, plan: CountGauss) -> torch.Tensor:
+    return CountGaussCsrFn.apply(vals, row_ptr, col_idx, plan)

@@ -1,0 +1,494 @@
+// cg_api.cu -- the C ABI of libcountgauss (declared in include/countgauss.h):
+// plans, argument validation, workspace layout and dispatch to the kernels.
+// Everything here is host code except the three generator-dump kernels.
+#include <new>
+#include <vector>
+
+#include "cg_internal.cuh"
+
+namespace cg {
+
+// Event pairs recorded per kernel kind; resolved and recycled by cg_plan_timing.
+struct TimingState {
+    std::vector<EventPair> pending[CG_KERNEL_COUNT];
+    std::vector<EventPair> free_pairs;
+    double carried_ms[CG_KERNEL_COUNT] = {0};
+    int64_t carried_launches[CG_KERNEL_COUNT] = {0};
+};
+
+namespace {
+
+constexpr size_t kMaxPendingPairs = 4096;
+
+void resolve(TimingState *ts, int kernel) {
+    for (EventPair &ev : ts->pending[kernel]) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(ev.stop) == cudaSuccess && cudaEventElapsedTime(&ms, ev.start, ev.stop) == cudaSuccess) {
+            ts->carried_ms[kernel] += ms;
+            ts->carried_launches[kernel] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        ts->free_pairs.push_back(ev);
+    }
+    ts->pending[kernel].clear();
+}
+
+}  // namespace
+
+const EventPair *timing_pair(cg_plan *p, int kernel) {
+    if (p == nullptr || !p->timing || kernel < 0 || kernel >= CG_KERNEL_COUNT) return nullptr;
+    TimingState *ts = static_cast<TimingState *>(p->timing_state);
+    if (ts == nullptr) {
+        ts = new (std::nothrow) TimingState;
+        if (ts == nullptr) return nullptr;
+        p->timing_state = ts;
+    }
+    if (ts->pending[kernel].size() >= kMaxPendingPairs) resolve(ts, kernel);
+    EventPair ev;
+    if (!ts->free_pairs.empty()) {
+        ev = ts->free_pairs.back();
+        ts->free_pairs.pop_back();
+    } else if (cudaEventCreate(&ev.start) != cudaSuccess || cudaEventCreate(&ev.stop) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    ts->pending[kernel].push_back(ev);
+    return &ts->pending[kernel].back();
+}
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+int g_sms[kMaxDevices] = {0};
+
+__global__ void generate_words_kernel(Key key, uint32_t tag, uint64_t idx0, int64_t count, uint32_t *words) {
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint4 w = stream_words(key, idx0 + static_cast<uint64_t>(t), tag);
+        reinterpret_cast<uint4 *>(words)[t] = w;
+    }
+}
+
+__global__ void generate_hash_sign_kernel(Key key, uint32_t B, int64_t row0, int64_t count, int32_t *h,
+                                          int32_t *sigma) {
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint32_t hh;
+        float s;
+        hash_sign(key, static_cast<uint64_t>(row0 + t), B, hh, s);
+        h[t] = static_cast<int32_t>(hh);
+        sigma[t] = s < 0.0f ? -1 : 1;
+    }
+}
+
+__global__ void generate_gaussian_kernel(Key key, uint32_t tag, int64_t R, int64_t r0, int64_t r1, int64_t c0,
+                                         int64_t c1, float *out) {
+    const int64_t rows = r1 - r0, cols = c1 - c0, total = rows * cols;
+    const uint64_t groups = static_cast<uint64_t>((R + 3) / 4);
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = r0 + t / cols;
+        const int64_t c = c0 + t % cols;
+        const float4 z = gauss_quad(key, tag, groups, static_cast<uint64_t>(c), static_cast<uint64_t>(r / 4));
+        const int lane = static_cast<int>(r & 3);
+        out[t] = lane == 0 ? z.x : lane == 1 ? z.y : lane == 2 ? z.z : z.w;
+    }
+}
+
+unsigned dump_grid(int64_t count) {
+    const int64_t g = (count + 255) / 256;
+    return static_cast<unsigned>(g < 1 ? 1 : (g > 65536 ? 65536 : g));
+}
+
+}  // namespace
+
+int num_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (dev < kMaxDevices && g_sms[dev] > 0) return g_sms[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (dev < kMaxDevices) g_sms[dev] = sms;
+    return sms;
+}
+
+cudaError_t launch_generate_words(Key key, uint32_t tag, uint64_t idx0, int64_t count, uint32_t *words,
+                                  cudaStream_t stream) {
+    generate_words_kernel<<<dump_grid(count), 256, 0, stream>>>(key, tag, idx0, count, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generate_hash_sign(Key key, uint32_t B, int64_t row0, int64_t count, int32_t *h, int32_t *sigma,
+                                      cudaStream_t stream) {
+    generate_hash_sign_kernel<<<dump_grid(count), 256, 0, stream>>>(key, B, row0, count, h, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generate_gaussian(Key key, uint32_t tag, int64_t R, int64_t r0, int64_t r1, int64_t c0,
+                                     int64_t c1, float *out, cudaStream_t stream) {
+    generate_gaussian_kernel<<<dump_grid((r1 - r0) * (c1 - c0)), 256, 0, stream>>>(key, tag, R, r0, r1, c0, c1,
+                                                                                  out);
+    return cudaGetLastError();
+}
+
+}  // namespace cg
+
+using namespace cg;
+
+namespace {
+
+constexpr int64_t kMaxRows = (1LL << 31) - 2;
+constexpr int64_t kMaxB = (1LL << 31) - 1;
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
+
+cg_status from_cuda(cudaError_t e) { return e == cudaSuccess ? CG_OK : CG_ERR_CUDA; }
+
+// Workspace layout: [status 256 B][region A][region B], each region 256-aligned.
+struct Layout {
+    size_t a_off = kStatusBytes, a_bytes = 0;
+    size_t b_off = 0, b_bytes = 0;
+    size_t total = 0;
+};
+
+Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
+    (void)nnz;
+    Layout L;
+    const size_t sx = static_cast<size_t>(p.B) * p.d * sizeof(float);
+    switch (op) {
+        case CG_OP_APPLY_CSR:
+        case CG_OP_APPLY_DENSE:
+            L.a_bytes = sx;
+            L.b_bytes = contract_partials_bytes(p);
+            break;
+        case CG_OP_CONTRACT:
+            L.b_bytes = contract_partials_bytes(p);
+            break;
+        case CG_OP_ADJOINT_DENSE:
+        case CG_OP_ADJOINT_CSR:
+            L.a_bytes = sx;
+            break;
+        case CG_OP_PLAIN_CSR:
+            L.b_bytes = static_cast<size_t>(plain_ctas(p.m, p.d)) * p.m * p.d * sizeof(float);
+            break;
+        case CG_OP_SKETCH:
+        default:
+            break;
+    }
+    L.b_off = L.a_off + align256(L.a_bytes);
+    L.total = L.b_off + align256(L.b_bytes);
+    return L;
+}
+
+cg_status check_ws(const cg_plan *p, int op, int64_t nnz, void *ws, size_t ws_bytes, Layout *L) {
+    *L = layout_for(*p, op, nnz);
+    if (ws == nullptr) return CG_ERR_INVALID_ARG;
+    if (misaligned(ws, 256)) return CG_ERR_INVALID_ARG;
+    if (ws_bytes < L->total) return CG_ERR_WORKSPACE;
+    return CG_OK;
+}
+
+cg_status check_csr(const cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                    int64_t nnz, bool need_vals) {
+    if (nnz < 0 || nnz > 0x7fffffffLL) return CG_ERR_INVALID_ARG;
+    if (row_ptr == nullptr) return CG_ERR_INVALID_ARG;
+    if (nnz > 0 && (col_idx == nullptr || (need_vals && vals == nullptr))) return CG_ERR_INVALID_ARG;
+    if (misaligned(row_ptr, 4) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
+    (void)p;
+    return CG_OK;
+}
+
+int *status_word(void *ws) { return reinterpret_cast<int *>(ws); }
+char *region(void *ws, size_t off) { return reinterpret_cast<char *>(ws) + off; }
+
+cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const Layout &L, cudaStream_t st) {
+    if (p->precision != CG_PREC_FP32) return CG_ERR_UNSUPPORTED;
+    return from_cuda(launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), contract_splits(*p),
+                                          reinterpret_cast<float *>(region(ws, L.b_off)), Y,
+                                          timing_pair(p, CG_KERNEL_CONTRACT), st));
+}
+
+cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                         int64_t nnz, float *SX, void *ws, cudaStream_t st) {
+    if (p->deterministic) return CG_ERR_UNSUPPORTED;
+    return from_cuda(launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
+                                              static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
+                                              p->row_offset, SX, status_word(ws), static_cast<int>(p->sketch_ctas),
+                                              timing_pair(p, CG_KERNEL_SKETCH), st));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cg_status_string(cg_status s) {
+    switch (s) {
+        case CG_OK: return "CG_OK";
+        case CG_ERR_INVALID_ARG: return "CG_ERR_INVALID_ARG: invalid argument";
+        case CG_ERR_UNSUPPORTED: return "CG_ERR_UNSUPPORTED: request not supported by this build";
+        case CG_ERR_WORKSPACE: return "CG_ERR_WORKSPACE: workspace too small";
+        case CG_ERR_CUDA: return "CG_ERR_CUDA: a CUDA call or kernel launch failed";
+        case CG_ERR_TIMEOUT: return "CG_ERR_TIMEOUT: a bounded device wait gave up";
+        case CG_ERR_DEVICE_BOUNDS: return "CG_ERR_DEVICE_BOUNDS: a kernel skipped an out-of-range index";
+        case CG_ERR_NO_DEVICE: return "CG_ERR_NO_DEVICE: no usable CUDA device";
+    }
+    return "unknown cg_status";
+}
+
+cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t seed, cg_plan **out) {
+    if (out == nullptr) return CG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 0 || n > kMaxRows || d < 1 || d > 65536 || m < 1 || m > 65536 || B < 1 || B > kMaxB)
+        return CG_ERR_INVALID_ARG;
+    if (B * static_cast<int64_t>(d) >= (1LL << 40)) return CG_ERR_INVALID_ARG;
+    cg_plan *p = new (std::nothrow) cg_plan;
+    if (p == nullptr) return CG_ERR_INVALID_ARG;
+    p->n = n;
+    p->d = d;
+    p->m = m;
+    p->B = B;
+    p->seed = seed;
+    p->precision = CG_PREC_FP32;
+    p->deterministic = 0;
+    p->row_offset = 0;
+    p->ksplit = 0;
+    p->sketch_ctas = 0;
+    p->timing = 0;
+    p->timing_state = nullptr;
+    *out = p;
+    return CG_OK;
+}
+
+cg_status cg_plan_destroy(cg_plan *plan) {
+    if (plan == nullptr) return CG_OK;
+    TimingState *ts = static_cast<TimingState *>(plan->timing_state);
+    if (ts != nullptr) {
+        for (int k = 0; k < CG_KERNEL_COUNT; ++k) {
+            for (EventPair &ev : ts->pending[k]) ts->free_pairs.push_back(ev);
+        }
+        for (EventPair &ev : ts->free_pairs) {
+            cudaEventDestroy(ev.start);
+            cudaEventDestroy(ev.stop);
+        }
+        delete ts;
+    }
+    delete plan;
+    return CG_OK;
+}
+
+cg_status cg_plan_timing(cg_plan *p, int32_t kernel, double *total_ms, int64_t *launches) {
+    if (p == nullptr || total_ms == nullptr || launches == nullptr || kernel < 0 || kernel >= CG_KERNEL_COUNT)
+        return CG_ERR_INVALID_ARG;
+    *total_ms = 0.0;
+    *launches = 0;
+    TimingState *ts = static_cast<TimingState *>(p->timing_state);
+    if (ts == nullptr) return CG_OK;
+    resolve(ts, kernel);
+    *total_ms = ts->carried_ms[kernel];
+    *launches = ts->carried_launches[kernel];
+    ts->carried_ms[kernel] = 0.0;
+    ts->carried_launches[kernel] = 0;
+    return CG_OK;
+}
+
+cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
+    if (p == nullptr) return CG_ERR_INVALID_ARG;
+    switch (option) {
+        case CG_OPT_PRECISION:
+            if (value < CG_PREC_FP32 || value > CG_PREC_FP8_E4M3) return CG_ERR_INVALID_ARG;
+            p->precision = static_cast<int32_t>(value);
+            return CG_OK;
+        case CG_OPT_DETERMINISTIC:
+            if (value != 0 && value != 1) return CG_ERR_INVALID_ARG;
+            p->deterministic = static_cast<int32_t>(value);
+            return CG_OK;
+        case CG_OPT_ROW_OFFSET:
+            if (value < 0 || value > (1LL << 62)) return CG_ERR_INVALID_ARG;
+            p->row_offset = value;
+            return CG_OK;
+        case CG_OPT_KSPLIT:
+            if (value < 0 || value > (1 << 20)) return CG_ERR_INVALID_ARG;
+            p->ksplit = value;
+            return CG_OK;
+        case CG_OPT_SKETCH_CTAS:
+            if (value < 0 || value > (1 << 20)) return CG_ERR_INVALID_ARG;
+            p->sketch_ctas = value;
+            return CG_OK;
+        case CG_OPT_TIMING:
+            if (value != 0 && value != 1) return CG_ERR_INVALID_ARG;
+            p->timing = static_cast<int32_t>(value);
+            return CG_OK;
+        default:
+            return CG_ERR_INVALID_ARG;
+    }
+}
+
+cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
+    if (p == nullptr || value == nullptr) return CG_ERR_INVALID_ARG;
+    switch (option) {
+        case CG_OPT_PRECISION: *value = p->precision; return CG_OK;
+        case CG_OPT_DETERMINISTIC: *value = p->deterministic; return CG_OK;
+        case CG_OPT_ROW_OFFSET: *value = p->row_offset; return CG_OK;
+        case CG_OPT_KSPLIT: *value = p->ksplit; return CG_OK;
+        case CG_OPT_SKETCH_CTAS: *value = p->sketch_ctas; return CG_OK;
+        case CG_OPT_TIMING: *value = p->timing; return CG_OK;
+        default: return CG_ERR_INVALID_ARG;
+    }
+}
+
+cg_status cg_workspace_size(const cg_plan *p, int32_t op, int64_t nnz, size_t *bytes) {
+    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_CONTRACT) return CG_ERR_INVALID_ARG;
+    *bytes = layout_for(*p, op, nnz).total;
+    return CG_OK;
+}
+
+cg_status cg_plan_check(const cg_plan *p, void *ws, void *stream) {
+    if (p == nullptr || ws == nullptr) return CG_ERR_INVALID_ARG;
+    int h = 0;
+    cudaStream_t st = as_stream(stream);
+    if (cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CG_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CG_ERR_CUDA;
+    if (h != 0) {
+        if (cudaMemsetAsync(ws, 0, sizeof(int), st) != cudaSuccess) return CG_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return CG_ERR_CUDA;
+    }
+    if (h & kStatusTimeout) return CG_ERR_TIMEOUT;
+    if (h & kStatusBounds) return CG_ERR_DEVICE_BOUNDS;
+    return CG_OK;
+}
+
+cg_status cg_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals, int64_t nnz,
+                        float *SX, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || SX == nullptr || misaligned(SX, 16)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
+    if (s != CG_OK) return s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_SKETCH, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    return run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, as_stream(stream));
+}
+
+cg_status cg_sketch_dense(cg_plan *p, const float *X, int64_t ldx, float *SX, void *ws, size_t ws_bytes,
+                          void *stream) {
+    if (p == nullptr || SX == nullptr || misaligned(SX, 16) || ldx < p->d) return CG_ERR_INVALID_ARG;
+    if (p->n > 0 && (X == nullptr || misaligned(X, 4))) return CG_ERR_INVALID_ARG;
+    cg_status s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_SKETCH, 0, ws, ws_bytes, &L)) != CG_OK) return s;
+    if (p->deterministic) return CG_ERR_UNSUPPORTED;
+    return from_cuda(launch_sketch_dense_atomic(X, ldx, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
+                                                make_key(p->seed), p->row_offset, SX, status_word(ws),
+                                                static_cast<int>(p->sketch_ctas), timing_pair(p, CG_KERNEL_SKETCH),
+                                                as_stream(stream)));
+}
+
+cg_status cg_contract(cg_plan *p, const float *SX, float *Y, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || SX == nullptr || Y == nullptr || misaligned(SX, 4) || misaligned(Y, 4))
+        return CG_ERR_INVALID_ARG;
+    cg_status s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_CONTRACT, 0, ws, ws_bytes, &L)) != CG_OK) return s;
+    return run_contract(p, SX, Y, ws, L, as_stream(stream));
+}
+
+cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals, int64_t nnz,
+                       float *Y, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
+    if (s != CG_OK) return s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_APPLY_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    if (p->precision != CG_PREC_FP32) return CG_ERR_UNSUPPORTED;
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    if ((s = run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, st)) != CG_OK) return s;
+    return run_contract(p, SX, Y, ws, L, st);
+}
+
+cg_status cg_apply_dense(cg_plan *p, const float *X, int64_t ldx, float *Y, void *ws, size_t ws_bytes,
+                         void *stream) {
+    if (p == nullptr || Y == nullptr || misaligned(Y, 4) || ldx < p->d) return CG_ERR_INVALID_ARG;
+    if (p->n > 0 && (X == nullptr || misaligned(X, 4))) return CG_ERR_INVALID_ARG;
+    cg_status s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_APPLY_DENSE, 0, ws, ws_bytes, &L)) != CG_OK) return s;
+    if (p->precision != CG_PREC_FP32 || p->deterministic) return CG_ERR_UNSUPPORTED;
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    s = from_cuda(launch_sketch_dense_atomic(X, ldx, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
+                                             make_key(p->seed), p->row_offset, SX, status_word(ws),
+                                             static_cast<int>(p->sketch_ctas), timing_pair(p, CG_KERNEL_SKETCH), st));
+    if (s != CG_OK) return s;
+    return run_contract(p, SX, Y, ws, L, st);
+}
+
+cg_status cg_apply_adjoint(cg_plan *p, const float *dY, const int32_t *row_ptr, const int32_t *col_idx, int64_t nnz,
+                           float *dX, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || dY == nullptr || misaligned(dY, 4) || misaligned(dX, 4)) return CG_ERR_INVALID_ARG;
+    const bool sparse = row_ptr != nullptr;
+    cg_status s;
+    if (sparse && (s = check_csr(p, row_ptr, col_idx, nullptr, nnz, false)) != CG_OK) return s;
+    if ((sparse ? nnz : p->n) > 0 && dX == nullptr) return CG_ERR_INVALID_ARG;
+    Layout L;
+    if ((s = check_ws(p, sparse ? CG_OP_ADJOINT_CSR : CG_OP_ADJOINT_DENSE, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    float *W = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    const Key key = make_key(p->seed);
+    if ((s = from_cuda(launch_adjoint_w(dY, p->m, p->d, p->B, key, W, timing_pair(p, CG_KERNEL_ADJOINT_W), st))) !=
+        CG_OK)
+        return s;
+    if (sparse)
+        return from_cuda(launch_gather_csr(W, row_ptr, col_idx, static_cast<int>(p->n), p->d,
+                                           static_cast<uint32_t>(p->B), static_cast<int>(nnz), key, p->row_offset,
+                                           dX, status_word(ws), timing_pair(p, CG_KERNEL_GATHER), st));
+    return from_cuda(launch_gather_dense(W, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), key,
+                                         p->row_offset, dX, timing_pair(p, CG_KERNEL_GATHER), st));
+}
+
+cg_status cg_plain_gaussian_apply(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                                  int64_t nnz, float *Y, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
+    if (s != CG_OK) return s;
+    if (!plain_supported(p->m, p->d)) return CG_ERR_UNSUPPORTED;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_PLAIN_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    return from_cuda(launch_plain_csr(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, p->m,
+                                      static_cast<int>(nnz), make_key(p->seed), p->row_offset,
+                                      reinterpret_cast<float *>(region(ws, L.b_off)), Y, status_word(ws),
+                                      timing_pair(p, CG_KERNEL_PLAIN), as_stream(stream)));
+}
+
+cg_status cg_generate_words(uint64_t seed, uint32_t tag, uint64_t idx0, int64_t count, uint32_t *words,
+                            void *stream) {
+    if (count < 0 || (count > 0 && (words == nullptr || misaligned(words, 16)))) return CG_ERR_INVALID_ARG;
+    if (count == 0) return CG_OK;
+    return from_cuda(launch_generate_words(make_key(seed), tag, idx0, count, words, as_stream(stream)));
+}
+
+cg_status cg_generate_hash_sign(uint64_t seed, int64_t B, int64_t row0, int64_t count, int32_t *h, int32_t *sigma,
+                                void *stream) {
+    if (count < 0 || B < 1 || B > kMaxB || row0 < 0) return CG_ERR_INVALID_ARG;
+    if (count > 0 && (h == nullptr || sigma == nullptr)) return CG_ERR_INVALID_ARG;
+    if (count == 0) return CG_OK;
+    return from_cuda(launch_generate_hash_sign(make_key(seed), static_cast<uint32_t>(B), row0, count, h, sigma,
+                                               as_stream(stream)));
+}
+
+cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
+                               float *out, void *stream) {
+    if (R < 1 || r0 < 0 || r1 < r0 || r1 > R || c0 < 0 || c1 < c0) return CG_ERR_INVALID_ARG;
+    if ((r1 - r0) * (c1 - c0) > 0 && out == nullptr) return CG_ERR_INVALID_ARG;
+    if ((r1 - r0) * (c1 - c0) == 0) return CG_OK;
+    return from_cuda(launch_generate_gaussian(make_key(seed), tag, R, r0, r1, c0, c1, out, as_stream(stream)));
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// cg_gauss.cu -- stage 2 of the transform: Y = G.SX with G (m x B, i.i.d. N(0,1),
+// Theorem 1) generated tile by tile in shared memory and never written to HBM
+// (Section 1.1: "computing G.(S.X) can now be done in O~(m^2 d^3) time").
+//
+// FP32 FFMA path.  The contraction dimension B is split over the grid ("split-K"):
+// CTA (s, bm, bn) owns a contiguous range of 32-column slabs of G, output rows
+// [64 bm, 64 bm + 64) and output columns [BN bn, BN bn + BN).  Per slab it draws the
+// 64 x 32 tile of G (one Philox call per 4 x 1 quad), stages the 32 x BN tile of
+// SX, and accumulates a 4 x TN register tile per thread.  When the output block is
+// smaller than 256 thread tiles, the surplus threads take interleaved k-indices of
+// the slab and are summed in a fixed order at the end.  Each CTA writes one m x d
+// partial; a second kernel sums the partials in a fixed order, so Y is
+// bit-reproducible for a given grid.
+#include <algorithm>
+
+#include "cg_internal.cuh"
+
+namespace cg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBM = 64;
+constexpr int kKT = 32;
+
+template <int TN>
+__global__ void __launch_bounds__(kThreads)
+contract_ffma_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_split,
+                     bool vec_x, float *__restrict__ part) {
+    constexpr int BN = 16 * TN;
+    constexpr int kMainFloats = kKT * (kBM + BN);
+    constexpr int kRedFloats = kThreads * 4 * TN;
+    constexpr int kRawFloats = kMainFloats > kRedFloats ? kMainFloats : kRedFloats;
+    __shared__ __align__(16) float raw[kRawFloats];
+    float(*sG)[kBM] = reinterpret_cast<float(*)[kBM]>(raw);                // [kKT][kBM]
+    float(*sX)[BN] = reinterpret_cast<float(*)[BN]>(raw + kKT * kBM);      // [kKT][BN]
+
+    const int split = blockIdx.x;
+    const int m0 = blockIdx.y * kBM;
+    const int n0 = blockIdx.z * BN;
+    const int bm = min(kBM, m - m0);
+    const int bn = min(BN, d - n0);
+    const int mt = (bm + 3) >> 2;
+    const int nt = (bn + TN - 1) / TN;
+    const int tiles = mt * nt;
+    const int kg = max(1, kThreads / tiles);
+    const int t = threadIdx.x;
+    const int tile = t % tiles;
+    const int grp = t / tiles;
+    const bool active = grp < kg;
+    const int ti = tile % mt;
+    const int tj = tile / mt;
+    const uint64_t groups = static_cast<uint64_t>((m + 3) >> 2);
+    const int g0 = m0 >> 2;
+
+    float acc[4][TN];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+
+    const int64_t nslabs = (B + kKT - 1) / kKT;
+    const int64_t s_begin = static_cast<int64_t>(split) * slabs_per_split;
+    const int64_t s_end = min(nslabs, s_begin + slabs_per_split);
+
+    for (int64_t sl = s_begin; sl < s_end; ++sl) {
+        const int64_t b0 = sl * kKT;
+        // G[m0 .. m0+4mt, b0 .. b0+kKT): quads of four rows of one column.
+        for (int q = t; q < mt * kKT; q += kThreads) {
+            const int gl = q % mt;
+            const int kk = q / mt;
+            const int64_t b = b0 + kk;
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (b < B) z = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(b), static_cast<uint64_t>(g0 + gl));
+            *reinterpret_cast<float4 *>(&sG[kk][4 * gl]) = z;
+        }
+        // SX[b0 .. b0+kKT, n0 .. n0+bn)
+        if (vec_x) {
+            constexpr int BQ = BN / 4;
+            for (int q = t; q < kKT * BQ; q += kThreads) {
+                const int kk = q / BQ;
+                const int cq = q % BQ;
+                const int64_t b = b0 + kk;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (b < B && 4 * cq < bn) x = __ldg(reinterpret_cast<const float4 *>(SX + b * d + n0) + cq);
+                *reinterpret_cast<float4 *>(&sX[kk][4 * cq]) = x;
+            }
+        } else {
+            for (int q = t; q < kKT * BN; q += kThreads) {
+                const int kk = q / BN;
+                const int cc = q % BN;
+                const int64_t b = b0 + kk;
+                sX[kk][cc] = (b < B && cc < bn) ? __ldg(SX + b * d + n0 + cc) : 0.0f;
+            }
+        }
+        __syncthreads();
+        if (active) {
+            for (int kk = grp; kk < kKT; kk += kg) {
+                const float4 a = *reinterpret_cast<const float4 *>(&sG[kk][4 * ti]);
+                float bv[TN];
+#pragma unroll
+                for (int j4 = 0; j4 < TN / 4; ++j4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(&sX[kk][TN * tj + 4 * j4]);
+                    bv[4 * j4 + 0] = x.x;
+                    bv[4 * j4 + 1] = x.y;
+                    bv[4 * j4 + 2] = x.z;
+                    bv[4 * j4 + 3] = x.w;
+                }
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    acc[0][j] = fmaf(a.x, bv[j], acc[0][j]);
+                    acc[1][j] = fmaf(a.y, bv[j], acc[1][j]);
+                    acc[2][j] = fmaf(a.z, bv[j], acc[2][j]);
+                    acc[3][j] = fmaf(a.w, bv[j], acc[3][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // Sum the k-groups in a fixed order (group 0 + group 1 + ...).
+    if (kg > 1) {
+        float *red = raw;
+        if (active && grp > 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) red[((grp - 1) * tiles + tile) * 4 * TN + i * TN + j] = acc[i][j];
+        }
+        __syncthreads();
+        if (grp == 0) {
+            for (int g = 1; g < kg; ++g)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] += red[((g - 1) * tiles + tile) * 4 * TN + i * TN + j];
+        }
+    }
+    if (grp == 0) {
+        float *out = part + static_cast<size_t>(split) * m * d;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = m0 + 4 * ti + i;
+            if (r >= m) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int c = n0 + TN * tj + j;
+                if (TN * tj + j < bn) out[static_cast<size_t>(r) * d + c] = acc[i][j];
+            }
+        }
+    }
+}
+
+// Y[o] = sum over s of part[s][o], s in increasing order within each of 8 lanes,
+// then the 8 lane sums in increasing lane order.
+__global__ void __launch_bounds__(256)
+reduce_splits_kernel(const float *__restrict__ part, int nsplit, int64_t total, float *__restrict__ Y) {
+    __shared__ float red[8][33];
+    const int lane = threadIdx.x & 31;
+    const int sl = threadIdx.x >> 5;
+    const int64_t o = static_cast<int64_t>(blockIdx.x) * 32 + lane;
+    float acc = 0.0f;
+    if (o < total) {
+        int s = sl;
+        for (; s + 24 < nsplit; s += 32) {
+            const float a0 = __ldg(part + static_cast<size_t>(s) * total + o);
+            const float a1 = __ldg(part + static_cast<size_t>(s + 8) * total + o);
+            const float a2 = __ldg(part + static_cast<size_t>(s + 16) * total + o);
+            const float a3 = __ldg(part + static_cast<size_t>(s + 24) * total + o);
+            acc += a0;
+            acc += a1;
+            acc += a2;
+            acc += a3;
+        }
+        for (; s < nsplit; s += 8) acc += __ldg(part + static_cast<size_t>(s) * total + o);
+    }
+    red[sl][lane] = acc;
+    __syncthreads();
+    if (sl == 0 && o < total) {
+        float r = red[0][lane];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) r += red[q][lane];
+        Y[o] = r;
+    }
+}
+
+}  // namespace
+
+int contract_splits(const cg_plan &p) {
+    const int64_t nslabs = (p.B + kKT - 1) / kKT;
+    if (p.ksplit > 0) return static_cast<int>(std::min<int64_t>(p.ksplit, nslabs));
+    const int TN = p.d > 64 ? 8 : 4;
+    const int64_t blocks = static_cast<int64_t>((p.m + kBM - 1) / kBM) * ((p.d + 16 * TN - 1) / (16 * TN));
+    const int sms = num_sms() > 0 ? num_sms() : 148;
+    const int64_t target = 3LL * sms;  // about three resident CTAs per SM
+    int64_t s = (target + blocks - 1) / blocks;
+    s = std::max<int64_t>(1, std::min<int64_t>(s, nslabs));
+    return static_cast<int>(s);
+}
+
+size_t contract_partials_bytes(const cg_plan &p) {
+    return static_cast<size_t>(contract_splits(p)) * p.m * p.d * sizeof(float);
+}
+
+cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream) {
+    if (total == 0) return cudaSuccess;
+    const int64_t grid = (total + 31) / 32;
+    reduce_splits_kernel<<<static_cast<unsigned>(grid), 256, 0, stream>>>(partials, nsplit, total, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials,
+                                 float *Y, const EventPair *ev, cudaStream_t stream) {
+    const int64_t nslabs = (B + kKT - 1) / kKT;
+    const int64_t per = (nslabs + nsplit - 1) / nsplit;
+    const int used = static_cast<int>((nslabs + per - 1) / per);
+    const int gm = (m + kBM - 1) / kBM;
+    const bool vec_x = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SX) & 15) == 0);
+    record(ev, true, stream);
+    if (d > 64) {
+        const int gn = (d + 127) / 128;
+        contract_ffma_kernel<8><<<dim3(used, gm, gn), kThreads, 0, stream>>>(SX, m, d, B, key, per, vec_x, partials);
+    } else {
+        const int gn = (d + 63) / 64;
+        contract_ffma_kernel<4><<<dim3(used, gm, gn), kThreads, 0, stream>>>(SX, m, d, B, key, per, vec_x, partials);
+    }
+    record(ev, false, stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream);
+}
+
+}  // namespace cg

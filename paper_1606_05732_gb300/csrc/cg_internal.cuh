@@ -1,0 +1,93 @@
+// cg_internal.cuh -- declarations shared by the translation units of libcountgauss.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/countgauss.h"
+#include "cg_rng.cuh"
+
+struct cg_plan {
+    int64_t n;
+    int32_t d;
+    int32_t m;
+    int64_t B;
+    uint64_t seed;
+    int32_t precision;      // cg_precision
+    int32_t deterministic;  // 0 / 1
+    int64_t row_offset;
+    int64_t ksplit;         // 0 = auto
+    int64_t sketch_ctas;    // 0 = auto
+    int32_t timing;         // CG_OPT_TIMING
+    void *timing_state;     // cg::TimingState*, created on first timed launch
+};
+
+namespace cg {
+
+// A pair of events recorded immediately before and after one kernel launch.
+struct EventPair {
+    cudaEvent_t start = nullptr;
+    cudaEvent_t stop = nullptr;
+};
+
+// Fresh event pair for a launch of `kernel` through plan p, or nullptr when timing
+// is off (cg_api.cu).
+const EventPair *timing_pair(cg_plan *p, int kernel);
+
+inline void record(const EventPair *ev, bool start, cudaStream_t s) {
+    if (ev != nullptr) cudaEventRecord(start ? ev->start : ev->stop, s);
+}
+
+// Device status word bits (first word of every workspace).
+constexpr int kStatusBounds = 1;
+constexpr int kStatusTimeout = 2;
+
+constexpr size_t kStatusBytes = 256;
+
+inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// SM count of the current device (cached per device).  Returns 0 without a device.
+int num_sms();
+
+// ---- scatter (cg_sketch.cu) -------------------------------------------------
+cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                     int ctas, const EventPair *ev, cudaStream_t stream);
+cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d, uint32_t B, Key key,
+                                       int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
+                                       cudaStream_t stream);
+int sketch_default_ctas();
+
+// ---- contraction (cg_gauss.cu) ----------------------------------------------
+int contract_splits(const cg_plan &p);
+size_t contract_partials_bytes(const cg_plan &p);
+cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials,
+                                 float *Y, const EventPair *ev, cudaStream_t stream);
+cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream);
+
+// ---- plain product (cg_plain.cu) ---------------------------------------------
+bool plain_supported(int m, int d);
+int plain_ctas(int m, int d);
+cudaError_t launch_plain_csr(const int *row_ptr, const int *col_idx, const float *vals, int n, int d, int m,
+                             int nnz, Key key, int64_t row_offset, float *partials, float *Y, int *status,
+                             const EventPair *ev, cudaStream_t stream);
+
+// ---- adjoint (cg_adjoint.cu) --------------------------------------------------
+cudaError_t launch_adjoint_w(const float *dY, int m, int d, int64_t B, Key key, float *W, const EventPair *ev,
+                             cudaStream_t stream);
+cudaError_t launch_gather_dense(const float *W, int n, int d, uint32_t B, Key key, int64_t row_offset, float *dX,
+                                const EventPair *ev, cudaStream_t stream);
+cudaError_t launch_gather_csr(const float *W, const int *row_ptr, const int *col_idx, int n, int d, uint32_t B,
+                              int nnz, Key key, int64_t row_offset, float *dXv, int *status, const EventPair *ev,
+                              cudaStream_t stream);
+
+// ---- generator dumps (cg_api.cu) ---------------------------------------------
+cudaError_t launch_generate_words(Key key, uint32_t tag, uint64_t idx0, int64_t count, uint32_t *words,
+                                  cudaStream_t stream);
+cudaError_t launch_generate_hash_sign(Key key, uint32_t B, int64_t row0, int64_t count, int32_t *h, int32_t *sigma,
+                                      cudaStream_t stream);
+cudaError_t launch_generate_gaussian(Key key, uint32_t tag, int64_t R, int64_t r0, int64_t r1, int64_t c0,
+                                     int64_t c1, float *out, cudaStream_t stream);
+
+}  // namespace cg

@@ -1,0 +1,80 @@
+// cg_rng.cuh -- device-side random streams of the CountGauss transform.
+//
+// The paper asks for independent uniform buckets and fair signs for the CountSketch
+// S (Section 1.1; Section 7) and i.i.d. unit-variance Gaussians for G and G~
+// (Section 2, Theorem 1).  Here they are pure functions of (seed, index), so no
+// random matrix is ever stored:
+//   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key (lo32(seed), hi32(seed)),
+//   counter (lo32(idx), hi32(idx), tag, 0).
+//   tag 0, idx = global row i:  h(i) = floor(w0 * B / 2^32),  sigma(i) = bit31(w1) ? -1 : +1.
+//   uniform u(w) = (2 (w >> 9) + 1) 2^-24, exact in fp32, never 0 or 1.
+//   Box-Muller quadruple of one call: sqrt(-2 ln u0) (cos, sin)(2 pi u1),
+//                                     sqrt(-2 ln u2) (cos, sin)(2 pi u3).
+//   Entry (r, c) of an R x C Gaussian with tag t: lane r%4 of the call at
+//   idx = c * ceil(R/4) + r/4 (tag 1: G, m x B; tag 2: G~, m x n).
+// The fp32 Box-Muller calls CUDA's logf, sqrtf and sincospif (exact argument
+// reduction of 2u); nothing here is compiled with fast-math.
+#pragma once
+#include <cstdint>
+
+namespace cg {
+
+constexpr uint32_t kTagHash = 0u;
+constexpr uint32_t kTagG = 1u;
+constexpr uint32_t kTagGTilde = 2u;
+
+struct Key {
+    uint32_t k0, k1;
+};
+
+__host__ __device__ __forceinline__ Key make_key(uint64_t seed) {
+    return Key{static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)};
+}
+
+// Ten Philox4x32 rounds: two 32x32->64 products per round (multipliers
+// 0xD2511F53, 0xCD9E8D57), key bumped by the Weyl constants 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox10(uint4 c, Key k) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t a = c.x, b = c.z;
+        const uint32_t hi_a = __umulhi(0xD2511F53u, a), lo_a = 0xD2511F53u * a;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, b), lo_b = 0xCD9E8D57u * b;
+        c = make_uint4(hi_b ^ c.y ^ k.k0, lo_b, hi_a ^ c.w ^ k.k1, lo_a);
+        k.k0 += 0x9E3779B9u;
+        k.k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 stream_words(Key k, uint64_t idx, uint32_t tag) {
+    return philox10(make_uint4(static_cast<uint32_t>(idx), static_cast<uint32_t>(idx >> 32), tag, 0u), k);
+}
+
+// Bucket and sign of global row i for a sketch with B rows (B < 2^32).
+__device__ __forceinline__ void hash_sign(Key k, uint64_t row, uint32_t B, uint32_t &h, float &s) {
+    const uint4 w = stream_words(k, row, kTagHash);
+    h = __umulhi(w.x, B);
+    s = (w.y & 0x80000000u) ? -1.0f : 1.0f;
+}
+
+__device__ __forceinline__ float uniform24(uint32_t w) {
+    return __uint2float_rn(((w >> 9) << 1) | 1u) * 5.9604644775390625e-8f;  // 2^-24
+}
+
+__device__ __forceinline__ float4 box_muller4(uint4 w) {
+    const float u0 = uniform24(w.x), u1 = uniform24(w.y);
+    const float u2 = uniform24(w.z), u3 = uniform24(w.w);
+    const float r01 = sqrtf(-2.0f * logf(u0));
+    const float r23 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    return make_float4(r01 * c1, r01 * s1, r23 * c3, r23 * s3);
+}
+
+// The four Gaussian entries (4g .. 4g+3, c) of an R x C Gaussian, groups = ceil(R/4).
+__device__ __forceinline__ float4 gauss_quad(Key k, uint32_t tag, uint64_t groups, uint64_t c, uint64_t g) {
+    return box_muller4(stream_words(k, c * groups + g, tag));
+}
+
+}  // namespace cg

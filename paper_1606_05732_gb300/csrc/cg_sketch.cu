@@ -1,0 +1,205 @@
+// cg_sketch.cu -- stage 1 of the transform: SX = S.X, the O(nnz(X)) CountSketch
+// scatter (Section 1.1: "computing S.X can be done in O(nnz(X)) time").
+//
+// Row i of X is added, times sigma(i), into row h(i) of SX (B x d, row-major fp32).
+// The scatter is one pass over the CSR arrays: every byte of row_ptr, col_idx and
+// vals is read once, with coalesced loads, and each nonzero becomes one fp32
+// reduction (RED) into SX, which the caller sizes to stay resident in L2.  The
+// bucket and sign of a row are recomputed from the Philox stream by the lane that
+// owns the row and shared through shared memory; nothing random is stored.
+#include "cg_internal.cuh"
+
+namespace cg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kUnroll = 4;  // nonzeros in flight per lane
+
+// One warp owns a chunk of 32 consecutive rows at a time.  Lane l hashes row l of
+// the chunk and loads its row_ptr entry; the chunk's nonzeros [beg, end) are then
+// swept 32 x kUnroll at a time with coalesced loads, and each nonzero finds its
+// row by a 5-step binary search over the chunk's 33 row offsets in shared memory.
+__global__ void __launch_bounds__(kThreads)
+sketch_csr_atomic_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                         const float *__restrict__ vals, int n, int d, uint32_t B, int nnz, Key key,
+                         int64_t row_offset, float *__restrict__ SX, int *__restrict__ status) {
+    __shared__ int s_rp[kWarps][33];
+    __shared__ uint32_t s_h[kWarps][32];
+    __shared__ float s_sg[kWarps][32];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int nchunks = (n + 31) >> 5;
+    int bad = 0;
+    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
+        const int first = c << 5;
+        const int i = first + lane;
+        const int last = min(first + 32, n);
+        const int end = __ldg(row_ptr + last);
+        int rp = end;
+        uint32_t h = 0;
+        float sg = 0.0f;
+        if (i < n) {
+            rp = __ldg(row_ptr + i);
+            hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+        }
+        s_rp[w][lane] = rp;
+        s_h[w][lane] = h;
+        s_sg[w][lane] = sg;
+        if (lane == 0) s_rp[w][32] = end;
+        __syncwarp();
+        const int beg = s_rp[w][0];
+        if (beg < 0 || end > nnz || beg > end) {  // malformed row_ptr: skip the chunk
+            bad = 1;
+            __syncwarp();
+            continue;
+        }
+        for (int k0 = beg; k0 < end; k0 += 32 * kUnroll) {
+            int col[kUnroll];
+            float v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int k = k0 + u * 32 + lane;
+                col[u] = -1;
+                v[u] = 0.0f;
+                if (k < end) {
+                    col[u] = __ldg(col_idx + k);
+                    v[u] = __ldg(vals + k);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int k = k0 + u * 32 + lane;
+                if (k < end) {
+                    int lo = 0;
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (s_rp[w][lo + step] <= k) lo += step;
+                    const int j = col[u];
+                    if (static_cast<unsigned>(j) < static_cast<unsigned>(d))
+                        atomicAdd(SX + static_cast<size_t>(s_h[w][lo]) * d + j, s_sg[w][lo] * v[u]);
+                    else
+                        bad = 1;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (bad) atomicOr(status, kStatusBounds);
+}
+
+// Dense X (n x d, row stride ldx), d % 4 == 0, ldx % 4 == 0, X 16-byte aligned:
+// a warp owns 32 rows at a time; lane l hashes row l; the 32 x d/4 float4 quads of
+// the rows are swept in row-major order (coalesced when ldx == d) and each is one
+// vector reduction into SX.
+__global__ void __launch_bounds__(kThreads)
+sketch_dense_vec4_kernel(const float *__restrict__ X, int64_t ldx, int n, int d, uint32_t B, Key key,
+                         int64_t row_offset, float *__restrict__ SX) {
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int nchunks = (n + 31) >> 5;
+    const int dq = d >> 2;
+    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
+        const int first = c << 5;
+        const int rows = min(32, n - first);
+        uint32_t h = 0;
+        float sg = 0.0f;
+        if (lane < rows) hash_sign(key, static_cast<uint64_t>(row_offset + first + lane), B, h, sg);
+        const int total = rows * dq;
+        for (int e0 = 0; e0 < total; e0 += 32 * kUnroll) {
+            float4 x[kUnroll];
+            int rr[kUnroll], qq[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int e = e0 + u * 32 + lane;
+                rr[u] = e / dq;
+                qq[u] = e - rr[u] * dq;
+                x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < total)
+                    x[u] = __ldg(reinterpret_cast<const float4 *>(X + (first + rr[u]) * ldx) + qq[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int e = e0 + u * 32 + lane;
+                const int src = min(rr[u], 31);
+                const uint32_t hh = __shfl_sync(0xffffffffu, h, src);
+                const float s = __shfl_sync(0xffffffffu, sg, src);
+                if (e < total) {
+                    float4 val = make_float4(s * x[u].x, s * x[u].y, s * x[u].z, s * x[u].w);
+                    atomicAdd(reinterpret_cast<float4 *>(SX + static_cast<size_t>(hh) * d) + qq[u], val);
+                }
+            }
+        }
+    }
+}
+
+// Dense X, any d and stride: scalar reductions.
+__global__ void __launch_bounds__(kThreads)
+sketch_dense_scalar_kernel(const float *__restrict__ X, int64_t ldx, int n, int d, uint32_t B, Key key,
+                           int64_t row_offset, float *__restrict__ SX) {
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int nchunks = (n + 31) >> 5;
+    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
+        const int first = c << 5;
+        const int rows = min(32, n - first);
+        uint32_t h = 0;
+        float sg = 0.0f;
+        if (lane < rows) hash_sign(key, static_cast<uint64_t>(row_offset + first + lane), B, h, sg);
+        const int64_t total = static_cast<int64_t>(rows) * d;
+        for (int64_t e0 = 0; e0 < total; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const int r = static_cast<int>(e / d < 31 ? e / d : 31);
+            const uint32_t hh = __shfl_sync(0xffffffffu, h, r);
+            const float s = __shfl_sync(0xffffffffu, sg, r);
+            if (e < total) {
+                const int j = static_cast<int>(e - static_cast<int64_t>(r) * d);
+                atomicAdd(SX + static_cast<size_t>(hh) * d + j, s * __ldg(X + (first + r) * ldx + j));
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int sketch_default_ctas() {
+    const int sms = num_sms();
+    return (sms > 0 ? sms : 148) * (2048 / kThreads);
+}
+
+cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                     int ctas, const EventPair *ev, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
+    if (e != cudaSuccess || n == 0) return e;
+    const int nchunks = (n + 31) / 32;
+    const int need = (nchunks + kWarps - 1) / kWarps;
+    const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
+    record(ev, true, stream);
+    sketch_csr_atomic_kernel<<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                            SX, status);
+    record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d, uint32_t B, Key key,
+                                       int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
+                                       cudaStream_t stream) {
+    (void)status;
+    cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
+    if (e != cudaSuccess || n == 0) return e;
+    const int nchunks = (n + 31) / 32;
+    const int need = (nchunks + kWarps - 1) / kWarps;
+    const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
+    const bool vec = (d % 4 == 0) && (ldx % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    record(ev, true, stream);
+    if (vec)
+        sketch_dense_vec4_kernel<<<grid, kThreads, 0, stream>>>(X, ldx, n, d, B, key, row_offset, SX);
+    else
+        sketch_dense_scalar_kernel<<<grid, kThreads, 0, stream>>>(X, ldx, n, d, B, key, row_offset, SX);
+    record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+}  // namespace cg

@@ -1,0 +1,114 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports every
+entry point that include/countgauss.h declares, and validates arguments on the
+host before launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1606_05732_gb300 import _lib
+from paper_1606_05732_gb300 import build as cgbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_symbols():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        names += re.findall(r"^CG_API\s+[\w\s\*]+?\b(cg_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cgbuild.build()
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ["cg_plan_create", "cg_plan_destroy", "cg_apply_csr", "cg_apply_dense", "cg_apply_adjoint",
+                     "cg_plain_gaussian_apply", "cg_workspace_size", "cg_plan_check", "cg_status_string"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding knows every one of them
+    bound = set(_lib.SIGNATURES) | {"cg_status_string"}
+    assert set(declared_symbols()) <= bound | set(getattr(_lib, "EXTRA_SYMBOLS", ())), \
+        set(declared_symbols()) - bound
+
+
+def test_library_is_built_for_sm103a():
+    obj = os.path.join(cgbuild.BUILD, "cg_sketch.o")
+    assert "-gencode" in cgbuild.ARCH and "arch=compute_103a,code=sm_103a" in cgbuild.ARCH
+    assert os.path.exists(obj)
+
+
+def _plan(lib, n=100, d=4, m=8, B=16, seed=1):
+    h = ctypes.c_void_p()
+    st = lib.cg_plan_create(n, d, m, B, seed, ctypes.byref(h))
+    return st, h
+
+
+def test_plan_validation(lib):
+    st, h = _plan(lib)
+    assert st == 0 and h.value
+    assert lib.cg_plan_destroy(h) == 0
+    for bad in [(-1, 4, 8, 16), (10, 0, 8, 16), (10, 4, 0, 16), (10, 4, 8, 0), (10, 4, 8, 1 << 31),
+                (10, 70000, 8, 16)]:
+        st, h = _plan(lib, *bad)
+        assert st == 1 and not h.value
+
+
+def test_options_and_workspace(lib):
+    st, h = _plan(lib)
+    val = ctypes.c_int64()
+    assert lib.cg_plan_set_option(h, 1, 2) == 0
+    assert lib.cg_plan_get_option(h, 1, ctypes.byref(val)) == 0 and val.value == 2
+    assert lib.cg_plan_set_option(h, 1, 9) == 1
+    assert lib.cg_plan_set_option(h, 99, 0) == 1
+    assert lib.cg_plan_set_option(h, 3, 12345) == 0
+    assert lib.cg_plan_get_option(h, 3, ctypes.byref(val)) == 0 and val.value == 12345
+    sz = ctypes.c_size_t()
+    for op in range(7):
+        assert lib.cg_workspace_size(h, op, 1000, ctypes.byref(sz)) == 0
+        assert sz.value >= 256 and sz.value % 256 == 0
+    assert lib.cg_workspace_size(h, 42, 0, ctypes.byref(sz)) == 1
+    lib.cg_plan_destroy(h)
+
+
+def test_host_side_argument_errors_launch_nothing(lib):
+    """Every one of these fails validation on the host, before any CUDA call."""
+    st, h = _plan(lib)
+    P = ctypes.c_void_p
+    fake = P(1 << 20)  # never dereferenced: validation rejects the call first
+    # null workspace
+    assert lib.cg_apply_csr(h, fake, fake, fake, 10, fake, P(0), 0, P(0)) == 1
+    # misaligned workspace
+    assert lib.cg_apply_csr(h, fake, fake, fake, 10, fake, P((1 << 20) + 8), 1 << 20, P(0)) == 1
+    # workspace too small
+    assert lib.cg_apply_csr(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
+    # negative nnz, nnz >= 2^31
+    assert lib.cg_apply_csr(h, fake, fake, fake, -1, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr(h, fake, fake, fake, 1 << 31, fake, fake, 1 << 30, P(0)) == 1
+    # null outputs / inputs
+    assert lib.cg_apply_csr(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr(h, P(0), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_dense(h, fake, 2, fake, fake, 1 << 30, P(0)) == 1  # ldx < d
+    assert lib.cg_generate_words(1, 0, 0, -5, fake, P(0)) == 1
+    assert lib.cg_generate_gaussian(1, 1, 8, 4, 2, 0, 3, fake, P(0)) == 1
+    assert lib.cg_plan_check(None, fake, P(0)) == 1
+    lib.cg_plan_destroy(h)
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        s = lib.cg_status_string(code).decode()
+        assert s.startswith("CG_")

@@ -1,0 +1,52 @@
+"""Parity at the benchmark sizes, in the launch configuration the benchmark uses.
+
+The CountGauss output is compared in full (the oracle sketches all nonzeros and
+contracts in FP64); the plain product G~.X is compared on sampled output rows,
+which the oracle computes row by row (row r of G~.X depends on row r of G~ only):
+the first and last group of four rows plus one more group.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_05732_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_workload(name):
+    from paper_1606_05732_gb300 import countgauss
+    X, w = synth.workload_csr(name)
+    dev = torch.device("cuda", 0)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).to(dev)
+    ci = torch.from_numpy(X.col_idx).to(dev)
+    v = torch.from_numpy(X.vals).to(dev)
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"])
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    Yp = plan.plain_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    del rp, ci, v
+    return X, w, Y, Yp
+
+
+@pytest.mark.parametrize("name", ["nmf_n16M_d64", "ladder_n64M_d128"])
+def test_fullsize_fp32(name):
+    X, w, Y, Yp = run_workload(name)
+    Yo = oracle.apply_csr(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals)
+    err = rel(Y, Yo)
+    print(f"{name}: CountGauss fp32 rel Frobenius error {err:.3e}")
+    assert err < FP32_TOL
+    rows = synth.sample_rows(w["m"], seed=w["seed"], groups=3)
+    Ypo = oracle.plain_csr(w["seed"], X.n, X.d, w["m"], X.row_ptr, X.col_idx, X.vals, rows=rows)
+    errp = rel(Yp[rows], Ypo)
+    print(f"{name}: plain fp32 rel Frobenius error on rows {rows.tolist()}: {errp:.3e}")
+    assert errp < FP32_TOL

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: bucket, sign and Philox words bit-exact; floating results within a relative
+Frobenius error of 1e-5 for the FP32 path.  Inputs are seeded and synthetic
+(paper_1606_05732_gb300.synth); expected values come from the oracle only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_05732_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def cg():
+    from paper_1606_05732_gb300 import countgauss
+    return countgauss
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def dev_csr(X):
+    return (torch.from_numpy(X.row_ptr.astype(np.int32)).cuda(),
+            torch.from_numpy(X.col_idx.astype(np.int32)).cuda(),
+            torch.from_numpy(X.vals.astype(np.float32)).cuda())
+
+
+# -----------------------------------------------------------------------------
+# Generator: bit-exact words, buckets and signs; Gaussians to fp32 rounding.
+# -----------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1, 3, 2**32 + 7, 2**64 - 1])
+@pytest.mark.parametrize("tag", [0, 1, 2])
+def test_words_bit_exact(seed, tag):
+    for idx0 in [0, 2**32 - 100, 2**40 + 3]:
+        got = cg().generate_words(seed, tag, idx0, 1000).cpu().numpy().view(np.uint32)
+        want = oracle.philox_words(seed, tag, idx0, 1000)
+        np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("B", [1, 3, 4096, 100003, 1 << 17, 1 << 18, (1 << 31) - 1])
+def test_hash_sign_bit_exact(B):
+    for seed, row0 in [(1, 0), (2, 12345), (2**63 + 5, 2**33)]:
+        h, s = cg().generate_hash_sign(seed, B, row0, 5000)
+        wh, ws = oracle.hash_sign(seed, B, row0, 5000)
+        np.testing.assert_array_equal(h.cpu().numpy(), wh)
+        np.testing.assert_array_equal(s.cpu().numpy(), ws)
+
+
+@pytest.mark.parametrize("tag,R", [(1, 8), (1, 13), (2, 128), (1, 1)])
+def test_gaussian_entries(tag, R):
+    got = cg().generate_gaussian(5, tag, R, 0, R, 1000, 1700).cpu().numpy()
+    want = oracle.gaussian_block(5, tag, R, 0, R, 1000, 1700)
+    # fp32 Box-Muller (logf, sqrtf, sincospif) against fp64: a few ulp of fp32
+    assert np.abs(got - want).max() < 4e-6 * max(1.0, np.abs(want).max())
+    assert rel(got, want) < 1e-6
+
+
+# -----------------------------------------------------------------------------
+# The transform, the plain product and the stages on shapes that span several
+# tiles and have ragged tails.
+# -----------------------------------------------------------------------------
+CASES = [
+    # n, d, m, B, seed, generator
+    (65536, 16, 8, 4096, 1, "bern0.05"),     # the small workload, full size
+    (5000, 64, 32, 2048, 2, "bern0.05u"),    # several tiles
+    (4099, 37, 13, 1000, 7, "ragged"),        # nothing a multiple of anything
+    (777, 128, 128, 4096, 3, "bern0.02"),    # d > 64 path, m = 128
+    (1, 1, 1, 1, 11, "ragged"),               # scalar
+    (300, 1, 5, 7, 12, "ragged"),              # d = 1
+    (2000, 5, 1, 64, 13, "ragged"),            # m = 1
+    (1000, 8, 70, 33, 14, "bern0.3"),          # m > 64, two row blocks
+    (100, 4, 4, 1, 15, "bern0.3"),             # B = 1
+    (64, 200, 9, 50, 16, "ragged"),            # d > 128, two column blocks
+]
+
+
+def make_input(n, d, seed, kind):
+    if kind == "ragged":
+        return synth.csr_ragged(n, d, seed=seed)
+    p = float(kind[4:].rstrip("u"))
+    return synth.csr_bernoulli(n, d, p, seed=seed, values="uniform" if kind.endswith("u") else "normal")
+
+
+@pytest.mark.parametrize("n,d,m,B,seed,kind", CASES)
+def test_apply_csr_parity(n, d, m, B, seed, kind):
+    X = make_input(n, d, seed, kind)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    rp, ci, v = dev_csr(X)
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL, rel(Y, Yo)
+
+
+@pytest.mark.parametrize("n,d,m,B,seed,kind", CASES)
+def test_plain_parity(n, d, m, B, seed, kind):
+    X = make_input(n, d, seed, kind)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    Y = plan.plain_csr(*dev_csr(X)).cpu().numpy()
+    plan.check()
+    Yo = oracle.plain_csr(seed, n, d, m, X.row_ptr, X.col_idx, X.vals)
+    assert rel(Y, Yo) < FP32_TOL, rel(Y, Yo)
+
+
+@pytest.mark.parametrize("n,d,m,B,seed", [(4099, 64, 32, 1024, 1), (1000, 37, 13, 100, 2), (333, 128, 64, 700, 3),
+                                          (50, 4, 4, 1, 4)])
+def test_apply_dense_parity(n, d, m, B, seed):
+    Xn = synth.dense_normal(n, d, seed=seed)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    X = torch.from_numpy(Xn).cuda()
+    Y = plan.apply_dense(X).cpu().numpy()
+    SX = plan.sketch_dense(X).cpu().numpy()
+    Yo, SXo = oracle.apply_dense(seed, m, B, Xn, return_sx=True)
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL
+
+
+def test_contract_alone_and_deterministic():
+    B, d, m, seed = 5000, 24, 20, 9
+    SXn = np.random.default_rng(0).standard_normal((B, d)).astype(np.float32)
+    plan = cg().CountGauss(10, d, m, B, seed)
+    SX = torch.from_numpy(SXn).cuda()
+    Y1 = plan.contract(SX).cpu().numpy()
+    Y2 = plan.contract(SX).cpu().numpy()
+    np.testing.assert_array_equal(Y1, Y2)  # fixed-order split-K reduction
+    assert rel(Y1, oracle.contract(seed, m, SXn)) < FP32_TOL
+
+
+def test_empty_inputs():
+    n, d, m, B = 200, 8, 8, 32
+    X = synth.csr_bernoulli(n, d, 0.0, seed=1)
+    plan = cg().CountGauss(n, d, m, B, 3)
+    rp, ci, v = dev_csr(X)
+    assert not plan.apply_csr(rp, ci, v).any()
+    assert not plan.plain_csr(rp, ci, v).any()
+    plan0 = cg().CountGauss(0, d, m, B, 3)
+    rp0 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    ev = torch.zeros(0, dtype=torch.float32, device="cuda")
+    assert not plan0.apply_csr(rp0, e, ev).any()
+    assert not plan0.plain_csr(rp0, e, ev).any()
+    plan0.check()
+
+
+def test_row_offset_shards_sum_to_whole():
+    """Shards with global row offsets (the distributed remark of Section 4)."""
+    n, d, m, B, seed = 10000, 16, 16, 512, 21
+    X = synth.csr_bernoulli(n, d, 0.1, seed=5)
+    whole = cg().CountGauss(n, d, m, B, seed).apply_csr(*dev_csr(X)).cpu().numpy().astype(np.float64)
+    whole_p = cg().CountGauss(n, d, m, B, seed).plain_csr(*dev_csr(X)).cpu().numpy().astype(np.float64)
+    acc = np.zeros_like(whole)
+    acc_p = np.zeros_like(whole_p)
+    cuts = [0, 3333, 3334, 9001, n]
+    for a, b in zip(cuts, cuts[1:]):
+        sub = synth.CSR(b - a, d, X.row_ptr[a:b + 1] - X.row_ptr[a], X.col_idx[X.row_ptr[a]:X.row_ptr[b]],
+                        X.vals[X.row_ptr[a]:X.row_ptr[b]])
+        plan = cg().CountGauss(b - a, d, m, B, seed, row_offset=a)
+        acc += plan.apply_csr(*dev_csr(sub)).cpu().numpy()
+        acc_p += plan.plain_csr(*dev_csr(sub)).cpu().numpy()
+    assert rel(acc, whole) < FP32_TOL
+    assert rel(acc_p, whole_p) < FP32_TOL
+
+
+# -----------------------------------------------------------------------------
+# Adjoint and autograd.
+# -----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,d,m,B,seed", [(4099, 64, 64, 1024, 4), (1000, 37, 13, 100, 2), (500, 128, 20, 333, 3)])
+def test_adjoint_parity(n, d, m, B, seed):
+    rng = np.random.default_rng(seed)
+    dYn = rng.standard_normal((m, d)).astype(np.float32)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    dY = torch.from_numpy(dYn).cuda()
+    dX = plan.adjoint(dY).cpu().numpy()
+    assert rel(dX, oracle.adjoint_dense(seed, n, m, B, dYn)) < FP32_TOL
+    X = synth.csr_ragged(n, d, seed=seed) if d < 100 else synth.csr_bernoulli(n, d, 0.05, seed=seed)
+    rp, ci, _ = dev_csr(X)
+    dXv = plan.adjoint(dY, rp, ci).cpu().numpy()
+    plan.check()
+    assert rel(dXv, oracle.adjoint_csr(seed, n, m, B, X.row_ptr, X.col_idx, dYn)) < FP32_TOL
+    # dot-product test on the device results: <T X, dY> = <X, T^T dY>
+    Xd = torch.from_numpy(synth.dense_normal(n, d, seed=seed + 1)).cuda()
+    lhs = float((plan.apply_dense(Xd).double() * dY.double()).sum())
+    rhs = float((Xd.double() * torch.from_numpy(dX).cuda().double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * max(1.0, abs(lhs))
+
+
+def test_autograd_dense_and_csr():
+    n, d, m, B, seed = 3000, 16, 8, 256, 6
+    plan = cg().CountGauss(n, d, m, B, seed)
+    X = torch.from_numpy(synth.dense_normal(n, d, seed=1)).cuda().requires_grad_(True)
+    dYn = np.random.default_rng(2).standard_normal((m, d)).astype(np.float32)
+    Y = cg().countgauss_dense(X, plan)
+    Y.backward(torch.from_numpy(dYn).cuda())
+    assert rel(X.grad.cpu().numpy(), oracle.adjoint_dense(seed, n, m, B, dYn)) < FP32_TOL
+    Xs = synth.csr_bernoulli(n, d, 0.1, seed=3)
+    rp, ci, v = dev_csr(Xs)
+    v = v.clone().requires_grad_(True)
+    Ys = cg().countgauss_csr(v, rp, ci, plan)
+    Ys.backward(torch.from_numpy(dYn).cuda())
+    assert rel(v.grad.cpu().numpy(), oracle.adjoint_csr(seed, n, m, B, Xs.row_ptr, Xs.col_idx, dYn)) < FP32_TOL
+
+
+def test_sketched_least_squares_gradient():
+    """Loss 1/2 ||T (X w - b)||^2: T applied to the d = 1 residual, gradient
+    X^T T^T T (X w - b), against the oracle."""
+    n, d, m, B, seed = 1 << 14, 64, 64, 1 << 12, 4
+    rng = np.random.default_rng(4)
+    Xn = rng.standard_normal((n, d)).astype(np.float32)
+    bn = rng.standard_normal((n, 1)).astype(np.float32)
+    wn = rng.standard_normal((d, 1)).astype(np.float32)
+    plan = cg().CountGauss(n, 1, m, B, seed)
+    X, b = torch.from_numpy(Xn).cuda(), torch.from_numpy(bn).cuda()
+    w = torch.from_numpy(wn).cuda().requires_grad_(True)
+    r = X @ w - b
+    loss = 0.5 * (cg().countgauss_dense(r, plan) ** 2).sum()
+    loss.backward()
+    r64 = Xn.astype(np.float64) @ wn.astype(np.float64) - bn.astype(np.float64)
+    Tr = oracle.apply_dense(seed, m, B, r64)
+    g = Xn.astype(np.float64).T @ oracle.adjoint_dense(seed, n, m, B, Tr)
+    assert abs(float(loss) - 0.5 * float(np.sum(Tr ** 2))) < 1e-4 * 0.5 * float(np.sum(Tr ** 2))
+    assert rel(w.grad.cpu().numpy(), g) < 1e-4  # X w - b in fp32 (torch) dominates
+
+
+# -----------------------------------------------------------------------------
+# Device bounds checks: a bad column index is skipped and reported, never used.
+# -----------------------------------------------------------------------------
+def test_bad_column_index_is_reported():
+    n, d, m, B = 100, 8, 4, 16
+    X = synth.csr_bernoulli(n, d, 0.5, seed=1)
+    ci = X.col_idx.copy()
+    ci[len(ci) // 2] = d + 5  # out of range: the kernels check before use
+    plan = cg().CountGauss(n, d, m, B, 1)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).cuda()
+    cit = torch.from_numpy(ci).cuda()
+    v = torch.from_numpy(X.vals).cuda()
+    plan.apply_csr(rp, cit, v)
+    with pytest.raises(cg()._lib.CountGaussError if hasattr(cg(), "_lib") else RuntimeError):
+        plan.check()
+    plan.check()  # cleared
+
+
+def test_argument_errors_raise():
+    plan = cg().CountGauss(10, 4, 4, 8, 1)
+    rp = torch.zeros(11, dtype=torch.int64, device="cuda")
+    with pytest.raises(TypeError):
+        plan.apply_csr(rp, rp.int(), torch.zeros(0, device="cuda"))
