@@ -28,9 +28,7 @@ import hashlib
 import json
 import os
 import statistics
-import subprocess
 import sys
-import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -48,7 +46,7 @@ NCU_TRAFFIC = {}
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -73,58 +71,77 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """SM clock and clock-event (throttle) reasons, read through NVML every 2 ms by a
+    background thread while the timed region runs (read-only queries)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.tmp = None
+    def __init__(self, torch_device):
+        self.dev = torch_device
+        self.samples = []
+        self.reasons = 0
+        self.max_mhz = None
+        self.error = None
+        self._stop = None
+        self._thread = None
+
+    def _open(self):
+        import ctypes
+        import torch
+        nvml = ctypes.CDLL("libnvidia-ml.so.1")
+        if nvml.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(self.dev)
+        bus = None
+        if all(hasattr(props, a) for a in ("pci_domain_id", "pci_bus_id", "pci_device_id")):
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0".encode()
+        if bus is None or nvml.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) != 0:
+            if nvml.nvmlDeviceGetHandleByIndex_v2(self.dev.index or 0, ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        c = ctypes.c_uint()
+        if nvml.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(c)) == 0:
+            self.max_mhz = float(c.value)
+        get_reasons = getattr(nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return nvml, h, get_reasons
 
     def __enter__(self):
+        import ctypes
+        import threading
         try:
-            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
+            nvml, h, get_reasons = self._open()
+        except Exception as e:  # noqa: BLE001
+            self.error = f"nvml unavailable: {e}"
+            return self
+        self._stop = threading.Event()
+
+        def poll():
+            c = ctypes.c_uint()
+            r = ctypes.c_ulonglong()
+            while not self._stop.is_set():
+                if nvml.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(c)) == 0:
+                    self.samples.append(float(c.value))
+                if get_reasons(h, ctypes.byref(r)) == 0:
+                    self.reasons |= int(r.value)
+                time.sleep(0.002)
+
+        self._thread = threading.Thread(target=poll, daemon=True)
+        self._thread.start()
         return self
 
     def __exit__(self, *exc):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
 
     def summary(self):
-        if self.proc is None or self.tmp is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.tmp.flush()
-        with open(self.tmp.name) as f:
-            rows = [ln.strip().split(",") for ln in f if ln.strip()]
-        os.unlink(self.tmp.name)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [x.strip() for x in r]
-            if len(r) < 9:
-                continue
-            try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, r[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        if self.error:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [self.error]}
+        names = [v for k, v in self.REASONS.items() if self.reasons & k]
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples)}
 
 
 def source_hash(*names):
@@ -225,7 +242,7 @@ def run_ours(args):
         pg.barrier()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(dev) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             step()
@@ -302,11 +319,16 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        t0 = time.perf_counter()
-        oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=0)
-        dt = time.perf_counter() - t0
+        reps, total = 0, 0.0
+        while reps < 1 or (total < 10.0 and reps < 20):
+            t0 = time.perf_counter()
+            oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=0)
+            total += time.perf_counter() - t0
+            reps += 1
+        dt = total / reps
         cpu = {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the full workload once (n={n}, nnz={nnz}), FP64, single thread, {dt:.1f} s"}
+               "sample": f"the full workload (n={n}, nnz={nnz}), FP64, single thread, mean of {reps} runs, "
+                         f"{dt:.2f} s each"}
 
     if rank == 0:
         line = {
