@@ -186,6 +186,35 @@ CG_API cg_status cg_sketch_dense(cg_plan *plan, const float *X, int64_t ldx, flo
 CG_API cg_status cg_contract(cg_plan *plan, const float *SX, float *Y,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* ---- without a workspace ------------------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they apply the transform (code inside an
+ * allocator or memory-pool callback, plugins handed only their input and output
+ * buffers by a host framework that owns every allocation, real-time loops that ban
+ * cudaMalloc/cudaFree after start-up).
+ *
+ * Same result as cg_apply_csr (FP32 precision, atomic scatter), but every piece of
+ * scratch (SX, the split-K partials, the status word) lives in one fixed device
+ * array of CG_NOALLOC_SCRATCH_BYTES inside the library, which each GPU that loads the
+ * library holds until the process exits.  The caller passes only inputs and Y.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any stream capture.
+ *   - Plans needing more than CG_NOALLOC_SCRATCH_BYTES of scratch (roughly
+ *     B.d.4 + splits.m.d.4 + 512 bytes) are rejected with CG_ERR_WORKSPACE; other
+ *     options return CG_ERR_UNSUPPORTED unless the plan is FP32 and not deterministic.
+ *   - All calls share the one array, which keeps the last call's contents (each call
+ *     clears what must start at zero).  Calls whose kernels overlap on the GPU (two
+ *     streams, or two host threads) race on it and corrupt each other's results:
+ *     serialise them, e.g. on one stream.
+ *   - Device-side bounds reports are not surfaced here; diagnose bad inputs with
+ *     cg_apply_csr and cg_plan_check. */
+#define CG_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+CG_API cg_status cg_apply_csr_noalloc(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
+                                      const float *vals, int64_t nnz, float *Y, void *stream);
+
 /* ---- the generator, exposed for bit-exact checks ---------------------------- */
 
 /* words[4t..4t+3] = Philox4x32-10 words of (seed, tag, idx0 + t), t < count

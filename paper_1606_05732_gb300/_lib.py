@@ -38,6 +38,7 @@ SIGNATURES = {
     "cg_plan_check": [P, P, P],
     "cg_plan_timing": [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
     "cg_apply_csr": [P, P, P, P, I64, P, P, SZ, P],
+    "cg_apply_csr_noalloc": [P, P, P, P, I64, P, P],
     "cg_apply_dense": [P, P, I64, P, P, SZ, P],
     "cg_apply_adjoint": [P, P, P, P, I64, P, P, SZ, P],
     "cg_plain_gaussian_apply": [P, P, P, P, I64, P, P, SZ, P],

@@ -1,0 +1,88 @@
+// cg_noalloc.cu -- cg_apply_csr_noalloc: the CSR transform with its scratch memory in a
+// fixed, file-scope device array instead of a caller-provided workspace.
+//
+// Some callers cannot allocate device memory at the point where they want the
+// transform: code running under an allocator that must not be re-entered (inside a
+// memory-pool callback or a custom allocator's own bookkeeping), plugins that are
+// handed only input and output buffers by a host framework that owns all device
+// allocations, and real-time loops that forbid cudaMalloc/cudaFree after start-up
+// because those calls can synchronise the device and take unbounded time.  For them
+// this entry point needs no workspace: the sketch SX, the split-K partials and the
+// status word live in `g_noalloc_scratch` below, which the CUDA runtime places in
+// device memory when the library's module is loaded on a device (every GPU that
+// loads the library holds these bytes until the process exits).
+//
+// Host code never dereferences `g_noalloc_scratch`: on the host the name denotes a
+// host-side shadow, not a device address, so its device address is looked up once
+// per device with cudaGetSymbolAddress (with that device current) and passed to the
+// kernels as a plain pointer.
+#include <mutex>
+
+#include "cg_internal.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = CG_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mutex;
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+cudaError_t scratch_address(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_scratch_ptr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) != 0; }
+
+}  // namespace
+
+extern "C" cg_status cg_apply_csr_noalloc(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx,
+                                          const float *vals, int64_t nnz, float *Y, void *stream) {
+    using namespace cg;
+    if (p == nullptr || Y == nullptr || row_ptr == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
+    if (nnz < 0 || nnz > 0x7fffffffLL) return CG_ERR_INVALID_ARG;
+    if (nnz > 0 && (col_idx == nullptr || vals == nullptr)) return CG_ERR_INVALID_ARG;
+    if (misaligned(row_ptr, 4) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
+    if (p->precision != CG_PREC_FP32 || p->deterministic) return CG_ERR_UNSUPPORTED;
+
+    // Scratch layout: [status 256 B][SX: B x d floats][split-K partials], 256-aligned.
+    const size_t sx_bytes = align256(static_cast<size_t>(p->B) * p->d * sizeof(float));
+    const int nsplit = contract_splits(*p);
+    const size_t part_bytes = align256(static_cast<size_t>(nsplit) * p->m * p->d * sizeof(float));
+    if (kStatusBytes + sx_bytes + part_bytes > kScratchBytes) return CG_ERR_WORKSPACE;
+
+    void *base = nullptr;
+    if (scratch_address(&base) != cudaSuccess) return CG_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *scratch = static_cast<char *>(base);
+    int *status = reinterpret_cast<int *>(scratch);
+    float *SX = reinterpret_cast<float *>(scratch + kStatusBytes);
+    float *partials = reinterpret_cast<float *>(scratch + kStatusBytes + sx_bytes);
+
+    // The array keeps the previous call's contents: the status word is cleared here,
+    // SX is cleared by the scatter launcher and the partials are fully overwritten.
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return CG_ERR_CUDA;
+    if (launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
+                                 static_cast<int>(nnz), make_key(p->seed), p->row_offset, SX, status,
+                                 static_cast<int>(p->sketch_ctas), nullptr, st) != cudaSuccess)
+        return CG_ERR_CUDA;
+    if (launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), nsplit, partials, Y, nullptr, st) !=
+        cudaSuccess)
+        return CG_ERR_CUDA;
+    return CG_OK;
+}
