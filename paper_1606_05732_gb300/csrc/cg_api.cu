@@ -211,6 +211,10 @@ int *status_word(void *ws) { return reinterpret_cast<int *>(ws); }
 char *region(void *ws, size_t off) { return reinterpret_cast<char *>(ws) + off; }
 
 cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const Layout &L, cudaStream_t st) {
+    if (p->precision == CG_PREC_BF16 || p->precision == CG_PREC_BF16X3)
+        return from_cuda(launch_contract_tc(SX, p->m, p->d, p->B, make_key(p->seed), p->precision,
+                                            contract_tc_splits(*p), reinterpret_cast<float *>(region(ws, L.b_off)),
+                                            Y, status_word(ws), timing_pair(p, CG_KERNEL_CONTRACT), st));
     if (p->precision != CG_PREC_FP32) return CG_ERR_UNSUPPORTED;
     return from_cuda(launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), contract_splits(*p),
                                           reinterpret_cast<float *>(region(ws, L.b_off)), Y,
@@ -406,7 +410,6 @@ cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_id
     if (s != CG_OK) return s;
     Layout L;
     if ((s = check_ws(p, CG_OP_APPLY_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
-    if (p->precision != CG_PREC_FP32) return CG_ERR_UNSUPPORTED;
     float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
     cudaStream_t st = as_stream(stream);
     if ((s = run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, st)) != CG_OK) return s;
@@ -420,7 +423,7 @@ cg_status cg_apply_dense(cg_plan *p, const float *X, int64_t ldx, float *Y, void
     cg_status s;
     Layout L;
     if ((s = check_ws(p, CG_OP_APPLY_DENSE, 0, ws, ws_bytes, &L)) != CG_OK) return s;
-    if (p->precision != CG_PREC_FP32 || p->deterministic) return CG_ERR_UNSUPPORTED;
+    if (p->deterministic) return CG_ERR_UNSUPPORTED;
     float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
     cudaStream_t st = as_stream(stream);
     s = from_cuda(launch_sketch_dense_atomic(X, ldx, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),

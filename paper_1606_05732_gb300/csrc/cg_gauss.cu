@@ -199,7 +199,8 @@ int contract_splits(const cg_plan &p) {
 }
 
 size_t contract_partials_bytes(const cg_plan &p) {
-    return static_cast<size_t>(contract_splits(p)) * p.m * p.d * sizeof(float);
+    const int splits = p.precision == CG_PREC_FP32 ? contract_splits(p) : contract_tc_splits(p);
+    return static_cast<size_t>(splits) * p.m * p.d * sizeof(float);
 }
 
 cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream) {

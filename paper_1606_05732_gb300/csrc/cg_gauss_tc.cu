@@ -1,0 +1,282 @@
+// cg_gauss_tc.cu -- stage 2 of the transform, Y = G.SX, on the 5th-generation tensor
+// cores: G (i.i.d. N(0,1), Theorem 1) is drawn by Box-Muller straight into shared
+// memory in the MMA operand layout and never touches HBM; SX is staged through
+// registers (fp32 -> bf16); tcgen05.mma accumulates in fp32 in tensor memory.
+//
+// Precisions (the "precision ladder"):
+//   bf16     Y ~= hi(G) . hi(SX)
+//   bf16x3   Y ~= hi(G).hi(SX) + hi(G).lo(SX) + lo(G).hi(SX), with lo(x) = bf16(x - hi(x));
+//            the dropped lo.lo term is about 2^-16 of each product.
+//
+// Tile: M = 128 rows of G (zero rows past m), N = NT columns of SX (64/128/256, zero
+// columns past d), K = 64 per slab (one 128-byte swizzle atom of bf16).  The CTA owns a
+// contiguous range of slabs of B (split-K); 2-stage ring: while the tensor core runs the
+// MMAs of slab i, the 256 threads draw G and convert SX for slab i+1.  Completion of a
+// stage's MMAs is signalled by tcgen05.commit on that stage's mbarrier.  The epilogue
+// reads the 128 x NT accumulator from TMEM and writes one fp32 partial per CTA; the
+// partials are summed in a fixed order by reduce_splits_kernel.
+//
+// Every wait is bounded (about two seconds of SM clock); on expiry the kernel sets
+// the timeout bit of the status word, stops issuing, waits (bounded) for MMAs in
+// flight, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "cg_internal.cuh"
+#include "cg_tc.cuh"
+
+namespace cg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kM = 128;
+constexpr int kBK = 64;
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ bool wait_stage(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void split_bf16(float x, float &hi, float &lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(x));
+    lo = x - hi;
+}
+
+template <int NT, bool SPLIT3>
+struct Cfg {
+    static constexpr uint32_t kA = kM * kBK * 2;  // 16 KB
+    static constexpr uint32_t kB = NT * kBK * 2;  // NT x 128 B
+    static constexpr uint32_t kStage = SPLIT3 ? 2 * (kA + kB) : (kA + kB);
+    static constexpr uint32_t kSmem = 2 * kStage + 1024;
+    static constexpr uint32_t kTmemCols = NT < 32 ? 32 : NT;
+};
+
+template <int NT, bool SPLIT3>
+__global__ void __launch_bounds__(kThreads, 1)
+contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_cta,
+                        float *__restrict__ part, int *__restrict__ status) {
+    using C = Cfg<NT, SPLIT3>;
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    const int lane = t & 31;
+    const uint32_t raw = tc::smem_u32(dsmem);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = dsmem + (sbase - raw);
+
+    const int m0 = blockIdx.z * kM;
+    const int n0 = blockIdx.y * NT;
+    const int bn = min(NT, d - n0);
+    const uint64_t groups = static_cast<uint64_t>((m + 3) >> 2);
+    const int64_t nslabs = (B + kBK - 1) / kBK;
+    const int64_t s_begin = static_cast<int64_t>(blockIdx.x) * slabs_per_cta;
+    const int64_t s_end = min(nslabs, s_begin + slabs_per_cta);
+    const int nmine = s_end > s_begin ? static_cast<int>(s_end - s_begin) : 0;
+
+    if (t == 0) {
+        tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
+        tc::fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), C::kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kM, NT);
+
+    int issued = 0;  // slabs whose MMAs were issued (thread 0's view == everyone's)
+    for (int it = 0; it < nmine; ++it) {
+        const int s = it & 1;
+        const int64_t k0 = (s_begin + it) * kBK;
+        if (it >= 2 && !wait_stage(tc::smem_u32(&mbar[s]), static_cast<uint32_t>(((it >> 1) - 1) & 1))) {
+            atomicOr(status, kStatusTimeout);
+            abort_flag = 1;
+        }
+        uint8_t *stage = gbase + s * C::kStage;
+        uint8_t *a_hi = stage;
+        uint8_t *b_hi = stage + C::kA;
+        uint8_t *a_lo = stage + C::kA + C::kB;
+        uint8_t *b_lo = a_lo + C::kA;
+
+        // A = G[m0 .. m0+128, k0 .. k0+64): blocks of 4 rows (one Philox call) x 4 columns.
+        for (int q = t; q < (kM / 4) * (kBK / 4); q += kThreads) {
+            const int gl = q >> 4;
+            const int kq = q & 15;
+            const uint64_t g = static_cast<uint64_t>((m0 >> 2) + gl);
+            float z[4][4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t col = k0 + 4 * kq + c;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < groups && col < B) v = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(col), g);
+                z[c][0] = v.x;
+                z[c][1] = v.y;
+                z[c][2] = v.z;
+                z[c][3] = v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = 4 * gl + r;
+                const bool live = m0 + row < m;
+                float h[4], l[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) split_bf16(live ? z[c][r] : 0.0f, h[c], l[c]);
+                const uint32_t off = tc::sw128_bf16(row, 4 * kq);
+                *reinterpret_cast<uint2 *>(a_hi + off) = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+                if (SPLIT3)
+                    *reinterpret_cast<uint2 *>(a_lo + off) =
+                        make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+            }
+        }
+        // B^T = SX[k0 .. k0+64, n0 .. n0+NT) stored [n][k].
+        for (int q = t; q < NT * (kBK / 4); q += kThreads) {
+            const int nl = q % NT;
+            const int kq = q / NT;
+            float h[4], l[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t krow = k0 + 4 * kq + c;
+                const float x = (krow < B && nl < bn) ? __ldg(SX + krow * d + n0 + nl) : 0.0f;
+                split_bf16(x, h[c], l[c]);
+            }
+            const uint32_t off = tc::sw128_bf16(nl, 4 * kq);
+            *reinterpret_cast<uint2 *>(b_hi + off) = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+            if (SPLIT3)
+                *reinterpret_cast<uint2 *>(b_lo + off) = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (abort_flag) break;
+        if (t == 0) {
+            tc::fence_after_sync();
+            const uint32_t sa_hi = sbase + s * C::kStage;
+            const uint32_t sb_hi = sa_hi + C::kA;
+            const uint32_t sa_lo = sa_hi + C::kA + C::kB;
+            const uint32_t sb_lo = sa_lo + C::kA;
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks) {
+                const uint32_t koff = 32u * ks;  // 16 bf16 of K = 32 bytes inside the swizzle atom
+                const uint64_t ad = tc::smem_desc_sw128(sa_hi + koff, 16, 1024);
+                const uint64_t bd = tc::smem_desc_sw128(sb_hi + koff, 16, 1024);
+                tc::mma_bf16(tmem, ad, bd, kIdesc, (it > 0 || ks > 0) ? 1u : 0u);
+                if (SPLIT3) {
+                    tc::mma_bf16(tmem, ad, tc::smem_desc_sw128(sb_lo + koff, 16, 1024), kIdesc, 1u);
+                    tc::mma_bf16(tmem, tc::smem_desc_sw128(sa_lo + koff, 16, 1024), bd, kIdesc, 1u);
+                }
+            }
+            tc::mma_commit(tc::smem_u32(&mbar[s]));
+        }
+        issued = it + 1;
+    }
+
+    // Wait for the last committed stage (commits complete in order).
+    bool ok = !abort_flag;
+    if (issued > 0) {
+        const int last = issued - 1;
+        if (!wait_stage(tc::smem_u32(&mbar[last & 1]), static_cast<uint32_t>((last >> 1) & 1))) {
+            atomicOr(status, kStatusTimeout);
+            ok = false;
+        }
+    }
+    tc::fence_after_sync();
+    __syncthreads();
+
+    // Epilogue: warps w and w+4 share TMEM lanes 32(w%4) .. +32 and split the columns.
+    const int quad = warp & 3;
+    const int half = warp >> 2;
+    const int row = quad * 32 + lane;
+    const int grow = m0 + row;
+    float *out = part + static_cast<size_t>(blockIdx.x) * m * d;
+    for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 32) {
+        uint32_t r[32];
+        tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0), r);
+        tc::tmem_ld_wait();
+        if (grow < m) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (c0 + j < bn)
+                    out[static_cast<size_t>(grow) * d + n0 + c0 + j] =
+                        (ok && issued > 0) ? __uint_as_float(r[j]) : 0.0f;
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::kTmemCols);
+}
+
+template <int NT, bool SPLIT3>
+cudaError_t launch_tc(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials, int *status,
+                      const EventPair *ev, cudaStream_t stream) {
+    using C = Cfg<NT, SPLIT3>;
+    const int64_t nslabs = (B + kBK - 1) / kBK;
+    const int64_t per = (nslabs + nsplit - 1) / nsplit;
+    const int used = static_cast<int>((nslabs + per - 1) / per);
+    // at least 120 KB of dynamic shared memory: one CTA per SM, so TMEM is never contended
+    const uint32_t smem = C::kSmem > 120u * 1024u ? C::kSmem : 120u * 1024u;
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_bf16_kernel<NT, SPLIT3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    dim3 grid(used, (d + NT - 1) / NT, (m + kM - 1) / kM);
+    record(ev, true, stream);
+    contract_tc_bf16_kernel<NT, SPLIT3><<<grid, kThreads, smem, stream>>>(SX, m, d, B, key, per, partials, status);
+    record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+int tc_nt(int d) { return d <= 64 ? 64 : (d <= 128 ? 128 : 256); }
+
+}  // namespace
+
+int contract_tc_splits(const cg_plan &p) {
+    const int64_t nslabs = (p.B + kBK - 1) / kBK;
+    if (p.ksplit > 0) return static_cast<int>(p.ksplit < nslabs ? p.ksplit : nslabs);
+    const int nt = tc_nt(p.d);
+    const int64_t blocks = static_cast<int64_t>((p.m + kM - 1) / kM) * ((p.d + nt - 1) / nt);
+    const int sms = num_sms() > 0 ? num_sms() : 148;
+    int64_t s = (sms + blocks - 1) / blocks;
+    if (s < 1) s = 1;
+    if (s > nslabs) s = nslabs;
+    return static_cast<int>(s);
+}
+
+cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
+                               float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream) {
+    cudaError_t e;
+    const int nt = tc_nt(d);
+    const bool x3 = precision == CG_PREC_BF16X3;
+    if (nt == 64)
+        e = x3 ? launch_tc<64, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
+               : launch_tc<64, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
+    else if (nt == 128)
+        e = x3 ? launch_tc<128, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
+               : launch_tc<128, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
+    else
+        e = x3 ? launch_tc<256, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
+               : launch_tc<256, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
+    if (e != cudaSuccess) return e;
+    const int64_t nslabs = (B + kBK - 1) / kBK;
+    const int64_t per = (nslabs + nsplit - 1) / nsplit;
+    const int used = static_cast<int>((nslabs + per - 1) / per);
+    return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream);
+}
+
+}  // namespace cg

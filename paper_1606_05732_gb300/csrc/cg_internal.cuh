@@ -66,6 +66,11 @@ cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key k
                                  float *Y, const EventPair *ev, cudaStream_t stream);
 cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream);
 
+// ---- tensor-core contraction (cg_gauss_tc.cu) -----------------------------------
+int contract_tc_splits(const cg_plan &p);
+cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
+                               float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream);
+
 // ---- plain product (cg_plain.cu) ---------------------------------------------
 bool plain_supported(int m, int d);
 int plain_ctas(int m, int d);

@@ -50,3 +50,26 @@ def test_fullsize_fp32(name):
     errp = rel(Yp[rows], Ypo)
     print(f"{name}: plain fp32 rel Frobenius error on rows {rows.tolist()}: {errp:.3e}")
     assert errp < FP32_TOL
+
+
+@pytest.fixture(scope="module")
+def ladder_case():
+    X, w = synth.workload_csr("ladder_n64M_d128")
+    Yo = oracle.apply_csr(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals)
+    return X, w, Yo
+
+
+@pytest.mark.parametrize("precision,bound", [("bf16x3", 1e-5), ("bf16", 2e-2)])
+def test_fullsize_precision_ladder(ladder_case, precision, bound):
+    from paper_1606_05732_gb300 import countgauss
+    X, w, Yo = ladder_case
+    dev = torch.device("cuda", 0)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).to(dev)
+    ci = torch.from_numpy(X.col_idx).to(dev)
+    v = torch.from_numpy(X.vals).to(dev)
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"], precision=precision)
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    err = rel(Y, Yo)
+    print(f"ladder_n64M_d128 {precision}: rel Frobenius error {err:.3e} (bound {bound})")
+    assert err < bound

@@ -1,0 +1,62 @@
+"""The precision ladder of the Gaussian contraction (tcgen05 tensor cores) against the
+FP64 oracle.  Bars: split-BF16x3 within the FP32 bar (relative Frobenius 1e-5);
+BF16 and FP8-E4M3 within the stated bound 2e-2, with the measured error printed."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_05732_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BOUND = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-2, "fp8": 2e-2}
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cg():
+    from paper_1606_05732_gb300 import countgauss
+    return countgauss
+
+
+SHAPES = [
+    # B, d, m, seed
+    (1 << 14, 128, 128, 3),   # one full 128 x 128 tile
+    (5000, 24, 20, 5),        # padding in M, N and the last K slab
+    (3000, 200, 130, 6),      # N tile 256, two M blocks
+    (64, 64, 8, 7),           # a single slab
+    (100003, 64, 32, 8),      # many slabs per CTA, ragged B
+]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("B,d,m,seed", SHAPES)
+def test_contract_ladder(precision, B, d, m, seed):
+    rng = np.random.default_rng(seed)
+    SXn = (rng.standard_normal((B, d)) * rng.uniform(0.1, 10.0, size=(1, d))).astype(np.float32)
+    plan = cg().CountGauss(10, d, m, B, seed, precision=precision)
+    Y = plan.contract(torch.from_numpy(SXn).cuda()).cpu().numpy()
+    plan.check()
+    err = rel(Y, oracle.contract(seed, m, SXn))
+    print(f"{precision} B={B} d={d} m={m}: rel Frobenius error {err:.3e}")
+    assert err < BOUND[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+def test_apply_csr_ladder(precision):
+    n, d, m, B, seed = 200000, 128, 128, 1 << 14, 3
+    X = synth.csr_bernoulli(n, d, 0.01, seed=seed)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).cuda()
+    ci = torch.from_numpy(X.col_idx).cuda()
+    v = torch.from_numpy(X.vals).cuda()
+    plan = cg().CountGauss(n, d, m, B, seed, precision=precision)
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    err = rel(Y, oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals))
+    print(f"apply_csr {precision}: rel Frobenius error {err:.3e}")
+    assert err < BOUND[precision]
