@@ -79,7 +79,9 @@ typedef enum cg_precision {
     CG_PREC_FP32 = 0,     /* FFMA, fp32 throughout */
     CG_PREC_BF16 = 1,     /* tcgen05 kind::f16, bf16 G and SX, fp32 accumulate in TMEM */
     CG_PREC_BF16X3 = 2,   /* split bf16: hi.hi + hi.lo + lo.hi, fp32 accumulate */
-    CG_PREC_FP8_E4M3 = 3  /* tcgen05 kind::f8f6f4, e4m3 with per-tile scales */
+    CG_PREC_FP8_E4M3 = 3, /* tcgen05 kind::f8f6f4, e4m3 with a per-tile scale for every 128 x N tile
+                             of SX (absmax / 448) and G quantised as e4m3(64 z) */
+    CG_PREC_FP8X3 = 4     /* split e4m3: hi.hi + hi.lo + lo.hi with the same per-tile scales */
 } cg_precision;
 
 typedef enum cg_option {

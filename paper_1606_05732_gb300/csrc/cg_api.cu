@@ -211,7 +211,7 @@ int *status_word(void *ws) { return reinterpret_cast<int *>(ws); }
 char *region(void *ws, size_t off) { return reinterpret_cast<char *>(ws) + off; }
 
 cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const Layout &L, cudaStream_t st) {
-    if (p->precision == CG_PREC_BF16 || p->precision == CG_PREC_BF16X3)
+    if (p->precision != CG_PREC_FP32)
         return from_cuda(launch_contract_tc(SX, p->m, p->d, p->B, make_key(p->seed), p->precision,
                                             contract_tc_splits(*p), reinterpret_cast<float *>(region(ws, L.b_off)),
                                             Y, status_word(ws), timing_pair(p, CG_KERNEL_CONTRACT), st));
@@ -308,7 +308,7 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
     if (p == nullptr) return CG_ERR_INVALID_ARG;
     switch (option) {
         case CG_OPT_PRECISION:
-            if (value < CG_PREC_FP32 || value > CG_PREC_FP8_E4M3) return CG_ERR_INVALID_ARG;
+            if (value < CG_PREC_FP32 || value > CG_PREC_FP8X3) return CG_ERR_INVALID_ARG;
             p->precision = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_DETERMINISTIC:

@@ -20,6 +20,7 @@
 // the timeout bit of the status word, stops issuing, waits (bounded) for MMAs in
 // flight, frees its TMEM and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "cg_internal.cuh"
 #include "cg_tc.cuh"
@@ -244,12 +245,270 @@ cudaError_t launch_tc(const float *SX, int m, int d, int64_t B, Key key, int nsp
 
 int tc_nt(int d) { return d <= 64 ? 64 : (d <= 128 ? 128 : 256); }
 
+// ---- FP8-E4M3 with per-tile scales -------------------------------------------------
+// K slab = one 128-byte swizzle atom of e4m3 = 128 columns of G / rows of SX.  Each
+// slab t is its own scaled tile: G is quantised as e4m3(64 z) (|64 z| <= 369 < 448,
+// exact power-of-two scale), the slab of SX as e4m3(x / s_t) with s_t = absmax / 448
+// over the 128 x NT tile.  Slab t's MMAs write a fresh fp32 tile D_t into TMEM buffer
+// t % 2; the epilogue warps then add D_t * s_t / 64 into registers while the tensor
+// core runs slab t + 1.  With SPLIT3 each operand is also split, x = hi + lo with
+// hi = e4m3(x), lo = e4m3(x - hi), and hi.hi + hi.lo + lo.hi is accumulated.
+constexpr int kBK8 = 128;
+constexpr float kGScale = 64.0f;
+constexpr float kE4M3Max = 448.0f;
+
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float e) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, e), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+__device__ __forceinline__ void split_e4m3(float x, float &hi, float &lo) {
+    const __nv_fp8_e4m3 h(x);
+    hi = static_cast<float>(h);
+    lo = x - hi;
+}
+
+template <int NT, bool SPLIT3>
+struct Cfg8 {
+    static constexpr uint32_t kA = kM * kBK8;   // 16 KB
+    static constexpr uint32_t kB = NT * kBK8;   // NT x 128 B
+    static constexpr uint32_t kStage = SPLIT3 ? 2 * (kA + kB) : (kA + kB);
+    static constexpr uint32_t kSmem = 2 * kStage + 1024;
+    static constexpr uint32_t kTmemCols = 2 * NT;  // two fp32 tiles
+    static constexpr int kQuadsPerThread = NT * (kBK8 / 4) / kThreads;
+};
+
+template <int NT, bool SPLIT3>
+__global__ void __launch_bounds__(kThreads, 1)
+contract_tc_fp8_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_cta,
+                       float *__restrict__ part, int *__restrict__ status) {
+    using C = Cfg8<NT, SPLIT3>;
+    extern __shared__ uint8_t dsmem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ float warp_max[kThreads / 32];
+    __shared__ float tile_scale[2];
+
+    const int t = threadIdx.x;
+    const int warp = t >> 5;
+    const int lane = t & 31;
+    const uint32_t raw = tc::smem_u32(dsmem);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = dsmem + (sbase - raw);
+
+    const int m0 = blockIdx.z * kM;
+    const int n0 = blockIdx.y * NT;
+    const int bn = min(NT, d - n0);
+    const uint64_t groups = static_cast<uint64_t>((m + 3) >> 2);
+    const int64_t nslabs = (B + kBK8 - 1) / kBK8;
+    const int64_t s_begin = static_cast<int64_t>(blockIdx.x) * slabs_per_cta;
+    const int64_t s_end = min(nslabs, s_begin + slabs_per_cta);
+    const int nmine = s_end > s_begin ? static_cast<int>(s_end - s_begin) : 0;
+
+    if (t == 0) {
+        tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
+        tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
+        tc::fence_mbar_init();
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&tmem_slot), C::kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    constexpr uint32_t kIdesc = tc::idesc_e4m3_f32(kM, NT);
+
+    const int quad = warp & 3;
+    const int half = warp >> 2;
+    const int row = quad * 32 + lane;
+    float acc[NT / 2];
+#pragma unroll
+    for (int j = 0; j < NT / 2; ++j) acc[j] = 0.0f;
+
+    // Add tile `tile` (TMEM buffer tile % 2) times its scale into acc.
+    auto drain = [&](int tile) {
+        const int b = tile & 1;
+        // warp-uniform outcome: tcgen05.ld below is .sync.aligned
+        const bool good = __all_sync(0xffffffffu, wait_stage(tc::smem_u32(&mbar[b]),
+                                                              static_cast<uint32_t>((tile >> 1) & 1)));
+        if (!good) {
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+            abort_flag = 1;
+            return;
+        }
+        tc::fence_after_sync();
+        const float sc = tile_scale[b] * (1.0f / kGScale);
+#pragma unroll
+        for (int c = 0; c < NT / 2; c += 32) {
+            uint32_t r[32];
+            tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quad * 32) << 16) +
+                                       static_cast<uint32_t>(b * NT + half * (NT / 2) + c),
+                                   r);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[c + j] = fmaf(__uint_as_float(r[j]), sc, acc[c + j]);
+        }
+    };
+
+    int issued = 0;
+    for (int it = 0; it < nmine; ++it) {
+        const int s = it & 1;
+        const int64_t k0 = (s_begin + it) * kBK8;
+        uint8_t *stage = gbase + s * C::kStage;
+        uint8_t *a_hi = stage;
+        uint8_t *b_hi = stage + C::kA;
+        uint8_t *a_lo = stage + C::kA + C::kB;
+        uint8_t *b_lo = a_lo + C::kA;
+
+        // SX slab into registers and its absmax.
+        float xb[C::kQuadsPerThread][4];
+        float amax = 0.0f;
+#pragma unroll
+        for (int j = 0; j < C::kQuadsPerThread; ++j) {
+            const int q = t + j * kThreads;
+            const int nl = q % NT;
+            const int kq = q / NT;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t krow = k0 + 4 * kq + c;
+                const float x = (krow < B && nl < bn) ? __ldg(SX + krow * d + n0 + nl) : 0.0f;
+                xb[j][c] = x;
+                amax = fmaxf(amax, fabsf(x));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (lane == 0) warp_max[warp] = amax;
+
+        // G slab: blocks of 4 rows (one Philox call) x 4 columns, quantised e4m3(64 z).
+        for (int q = t; q < (kM / 4) * (kBK8 / 4); q += kThreads) {
+            const int gl = q >> 5;
+            const int kq = q & 31;
+            const uint64_t g = static_cast<uint64_t>((m0 >> 2) + gl);
+            float z[4][4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t col = k0 + 4 * kq + c;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < groups && col < B) v = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(col), g);
+                z[c][0] = v.x;
+                z[c][1] = v.y;
+                z[c][2] = v.z;
+                z[c][3] = v.w;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int rr = 4 * gl + r;
+                const bool live = m0 + rr < m;
+                float h[4], l[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) split_e4m3(live ? kGScale * z[c][r] : 0.0f, h[c], l[c]);
+                const uint32_t off = tc::sw128_b8(rr, 4 * kq);
+                *reinterpret_cast<uint32_t *>(a_hi + off) = pack_e4m3x4(h[0], h[1], h[2], h[3]);
+                if (SPLIT3) *reinterpret_cast<uint32_t *>(a_lo + off) = pack_e4m3x4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        __syncthreads();  // warp_max complete; also: every thread finished draining tile it-2
+        float tmax = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) tmax = fmaxf(tmax, warp_max[w]);
+        const float scale = tmax > 0.0f ? tmax / kE4M3Max : 1.0f;
+        const float inv = 1.0f / scale;
+        if (t == 0) tile_scale[s] = scale;
+#pragma unroll
+        for (int j = 0; j < C::kQuadsPerThread; ++j) {
+            const int q = t + j * kThreads;
+            const int nl = q % NT;
+            const int kq = q / NT;
+            float h[4], l[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) split_e4m3(xb[j][c] * inv, h[c], l[c]);
+            const uint32_t off = tc::sw128_b8(nl, 4 * kq);
+            *reinterpret_cast<uint32_t *>(b_hi + off) = pack_e4m3x4(h[0], h[1], h[2], h[3]);
+            if (SPLIT3) *reinterpret_cast<uint32_t *>(b_lo + off) = pack_e4m3x4(l[0], l[1], l[2], l[3]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (abort_flag) break;
+        if (t == 0) {
+            tc::fence_after_sync();
+            const uint32_t sa_hi = sbase + s * C::kStage;
+            const uint32_t sb_hi = sa_hi + C::kA;
+            const uint32_t sa_lo = sa_hi + C::kA + C::kB;
+            const uint32_t sb_lo = sa_lo + C::kA;
+            const uint32_t dst = tmem + static_cast<uint32_t>(s * NT);
+#pragma unroll
+            for (int ks = 0; ks < kBK8 / 32; ++ks) {
+                const uint32_t koff = 32u * ks;  // 32 e4m3 of K = 32 bytes
+                const uint64_t ad = tc::smem_desc_sw128(sa_hi + koff, 16, 1024);
+                const uint64_t bd = tc::smem_desc_sw128(sb_hi + koff, 16, 1024);
+                tc::mma_e4m3(dst, ad, bd, kIdesc, ks > 0 ? 1u : 0u);
+                if (SPLIT3) {
+                    tc::mma_e4m3(dst, ad, tc::smem_desc_sw128(sb_lo + koff, 16, 1024), kIdesc, 1u);
+                    tc::mma_e4m3(dst, tc::smem_desc_sw128(sa_lo + koff, 16, 1024), bd, kIdesc, 1u);
+                }
+            }
+            tc::mma_commit(tc::smem_u32(&mbar[s]));
+        }
+        issued = it + 1;
+        if (it >= 1) drain(it - 1);
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+    if (issued > 0 && !abort_flag) drain(issued - 1);
+    __syncthreads();
+    // A drained tile leaves no MMA in flight; after an abort wait (bounded) for the
+    // last issued tile before TMEM is released.
+    if (abort_flag && issued > 0) wait_stage(tc::smem_u32(&mbar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1);
+    const bool ok = !abort_flag;
+    const int grow = m0 + row;
+    float *out = part + static_cast<size_t>(blockIdx.x) * m * d;
+    if (grow < m) {
+#pragma unroll
+        for (int j = 0; j < NT / 2; ++j) {
+            const int c = half * (NT / 2) + j;
+            if (c < bn) out[static_cast<size_t>(grow) * d + n0 + c] = ok ? acc[j] : 0.0f;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::kTmemCols);
+}
+
+template <int NT, bool SPLIT3>
+cudaError_t launch_tc8(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials, int *status,
+                       const EventPair *ev, cudaStream_t stream) {
+    using C = Cfg8<NT, SPLIT3>;
+    const int64_t nslabs = (B + kBK8 - 1) / kBK8;
+    const int64_t per = (nslabs + nsplit - 1) / nsplit;
+    const int used = static_cast<int>((nslabs + per - 1) / per);
+    const uint32_t smem = C::kSmem > 120u * 1024u ? C::kSmem : 120u * 1024u;
+    cudaError_t e = cudaFuncSetAttribute(contract_tc_fp8_kernel<NT, SPLIT3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    dim3 grid(used, (d + NT - 1) / NT, (m + kM - 1) / kM);
+    record(ev, true, stream);
+    contract_tc_fp8_kernel<NT, SPLIT3><<<grid, kThreads, smem, stream>>>(SX, m, d, B, key, per, partials, status);
+    record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+int tc8_nt(int d) { return d <= 64 ? 64 : 128; }
+
 }  // namespace
 
 int contract_tc_splits(const cg_plan &p) {
-    const int64_t nslabs = (p.B + kBK - 1) / kBK;
+    const bool fp8 = p.precision == CG_PREC_FP8_E4M3 || p.precision == CG_PREC_FP8X3;
+    const int64_t bk = fp8 ? kBK8 : kBK;
+    const int64_t nslabs = (p.B + bk - 1) / bk;
     if (p.ksplit > 0) return static_cast<int>(p.ksplit < nslabs ? p.ksplit : nslabs);
-    const int nt = tc_nt(p.d);
+    const int nt = fp8 ? tc8_nt(p.d) : tc_nt(p.d);
     const int64_t blocks = static_cast<int64_t>((p.m + kM - 1) / kM) * ((p.d + nt - 1) / nt);
     const int sms = num_sms() > 0 ? num_sms() : 148;
     int64_t s = (sms + blocks - 1) / blocks;
@@ -261,9 +520,17 @@ int contract_tc_splits(const cg_plan &p) {
 cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
                                float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream) {
     cudaError_t e;
-    const int nt = tc_nt(d);
-    const bool x3 = precision == CG_PREC_BF16X3;
-    if (nt == 64)
+    const bool fp8 = precision == CG_PREC_FP8_E4M3 || precision == CG_PREC_FP8X3;
+    const int nt = fp8 ? tc8_nt(d) : tc_nt(d);
+    const bool x3 = precision == CG_PREC_BF16X3 || precision == CG_PREC_FP8X3;
+    if (fp8) {
+        if (nt == 64)
+            e = x3 ? launch_tc8<64, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
+                   : launch_tc8<64, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
+        else
+            e = x3 ? launch_tc8<128, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
+                   : launch_tc8<128, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
+    } else if (nt == 64)
         e = x3 ? launch_tc<64, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
                : launch_tc<64, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
     else if (nt == 128)
@@ -273,7 +540,8 @@ cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key
         e = x3 ? launch_tc<256, true>(SX, m, d, B, key, nsplit, partials, status, ev, stream)
                : launch_tc<256, false>(SX, m, d, B, key, nsplit, partials, status, ev, stream);
     if (e != cudaSuccess) return e;
-    const int64_t nslabs = (B + kBK - 1) / kBK;
+    const int64_t bk = fp8 ? kBK8 : kBK;
+    const int64_t nslabs = (B + bk - 1) / bk;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
     return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream);

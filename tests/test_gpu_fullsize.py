@@ -59,7 +59,7 @@ def ladder_case():
     return X, w, Yo
 
 
-@pytest.mark.parametrize("precision,bound", [("bf16x3", 1e-5), ("bf16", 2e-2)])
+@pytest.mark.parametrize("precision,bound", [("bf16x3", 1e-5), ("bf16", 2e-2), ("fp8x3", 2e-2), ("fp8", 5e-2)])
 def test_fullsize_precision_ladder(ladder_case, precision, bound):
     from paper_1606_05732_gb300 import countgauss
     X, w, Yo = ladder_case
