@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scatter", choices=["auto", "atomic", "partition"], default="auto")
     return ap.parse_args()
 
 
@@ -222,7 +223,10 @@ def run_ours(args):
     ci_h = torch.from_numpy(X.col_idx).pin_memory()
     v_h = torch.from_numpy(X.vals).pin_memory()
     rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
-    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n)
+    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter)
+    partitioned = args.scatter != "atomic"  # auto picks the partitioned scatter for this workload
+    scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_atomic_kernel")
+    scatter_src = ("cg_sketch_part.cu", "cg_rng.cuh") if partitioned else ("cg_sketch.cu", "cg_rng.cuh")
     Y = torch.empty(m, d, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -267,7 +271,7 @@ def run_ours(args):
     alg_bytes = 8 * nnz + 4 * (n + 1) + 4 * B * d
     sketch_avg_s = (sketch_ms / max(1, sketch_n)) / 1e3
     achieved = alg_bytes / sketch_avg_s / 1e9
-    src = source_hash("cg_sketch.cu", "cg_rng.cuh")
+    src = source_hash(*scatter_src)
     traffic = NCU_TRAFFIC.get(src)
 
     # plain G~.X on the same input
@@ -338,7 +342,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "n": n, "d": d, "p": wl["p"], "values": wl["values"],
                        "nnz_per_rank": nnz, "m": m, "B": B, "seed": seed,
                        "l2": "CSR inputs (%.0f MB) exceed L2; no flush" % (h2d / 1e6)},
-            "roofline": {"kernel": "sketch_csr_atomic_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "roofline": {"kernel": scatter_kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sketch_avg_s * 1e3,
                          "launches": sketch_n},

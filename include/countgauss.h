@@ -91,8 +91,11 @@ typedef enum cg_option {
     CG_OPT_ROW_OFFSET = 3,    /* global index of local row 0 (default 0) */
     CG_OPT_KSPLIT = 4,        /* CTAs along B in the contraction; 0 = automatic */
     CG_OPT_SKETCH_CTAS = 5,   /* CTAs of the scatter kernel; 0 = automatic */
-    CG_OPT_TIMING = 6         /* 1: record CUDA events around each main kernel launch
+    CG_OPT_TIMING = 6,        /* 1: record CUDA events around each main kernel launch
                                  (read with cg_plan_timing); 0 (default): off */
+    CG_OPT_SCATTER = 7        /* CSR scatter algorithm (atomic mode): 0 = automatic (default),
+                                 1 = one L2 reduction per nonzero, 2 = partition the nonzeros by
+                                 bucket range and accumulate each range in shared memory */
 } cg_option;
 
 typedef enum cg_kernel {

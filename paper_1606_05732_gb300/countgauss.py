@@ -47,7 +47,8 @@ class CountGauss:
     """A CountGauss plan T = G.S for X of n rows and d columns (cg_plan_create)."""
 
     def __init__(self, n: int, d: int, m: int, B: int, seed: int, *, precision: str = "fp32",
-                 deterministic: bool = False, row_offset: int = 0, ksplit: int = 0, sketch_ctas: int = 0):
+                 deterministic: bool = False, row_offset: int = 0, ksplit: int = 0, sketch_ctas: int = 0,
+                 scatter: str = "auto"):
         lib = _lib.load()
         h = _P()
         _lib.check("cg_plan_create", lib.cg_plan_create(n, d, m, B, seed, ctypes.byref(h)))
@@ -60,6 +61,7 @@ class CountGauss:
         self.set_option(_lib.OPT_ROW_OFFSET, int(row_offset))
         self.set_option(_lib.OPT_KSPLIT, int(ksplit))
         self.set_option(_lib.OPT_SKETCH_CTAS, int(sketch_ctas))
+        self.set_option(_lib.OPT_SCATTER, _lib.SCATTER[scatter])
         self.precision = precision
         self.deterministic = bool(deterministic)
         self.row_offset = int(row_offset)

@@ -153,19 +153,36 @@ bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t
 
 cg_status from_cuda(cudaError_t e) { return e == cudaSuccess ? CG_OK : CG_ERR_CUDA; }
 
-// Workspace layout: [status 256 B][region A][region B], each region 256-aligned.
+// Whether a CSR scatter through plan p uses the partitioned algorithm: always in
+// deterministic mode (exact fixed-point accumulation), on request otherwise (the
+// default atomic scatter is faster at present).
+bool use_partition(const cg_plan &p) {
+    if (p.deterministic) return partition_supported(p);
+    return p.scatter == 2 && partition_supported(p);
+}
+
+// Workspace layout: [status 256 B][region A][region B][region C], each 256-aligned.
+// A: SX or W;  B: split-K partials;  C: scratch of the partitioned scatter.
 struct Layout {
     size_t a_off = kStatusBytes, a_bytes = 0;
     size_t b_off = 0, b_bytes = 0;
+    size_t c_off = 0, c_bytes = 0;
     size_t total = 0;
+    PartLayout part;
 };
 
 Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
-    (void)nnz;
     Layout L;
     const size_t sx = static_cast<size_t>(p.B) * p.d * sizeof(float);
     switch (op) {
         case CG_OP_APPLY_CSR:
+            L.a_bytes = sx;
+            L.b_bytes = contract_partials_bytes(p);
+            if (use_partition(p)) {
+                L.part = partition_layout(p, nnz);
+                L.c_bytes = L.part.bytes;
+            }
+            break;
         case CG_OP_APPLY_DENSE:
             L.a_bytes = sx;
             L.b_bytes = contract_partials_bytes(p);
@@ -181,11 +198,17 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
             L.b_bytes = static_cast<size_t>(plain_ctas(p.m, p.d)) * p.m * p.d * sizeof(float);
             break;
         case CG_OP_SKETCH:
+            if (use_partition(p)) {
+                L.part = partition_layout(p, nnz);
+                L.c_bytes = L.part.bytes;
+            }
+            break;
         default:
             break;
     }
     L.b_off = L.a_off + align256(L.a_bytes);
-    L.total = L.b_off + align256(L.b_bytes);
+    L.c_off = L.b_off + align256(L.b_bytes);
+    L.total = L.c_off + align256(L.c_bytes);
     return L;
 }
 
@@ -222,8 +245,13 @@ cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const La
 }
 
 cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
-                         int64_t nnz, float *SX, void *ws, cudaStream_t st) {
-    if (p->deterministic) return CG_ERR_UNSUPPORTED;
+                         int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st) {
+    if (p->deterministic && !use_partition(*p)) return CG_ERR_UNSUPPORTED;
+    if (use_partition(*p))
+        return from_cuda(launch_sketch_csr_partitioned(
+            row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), static_cast<int>(nnz),
+            make_key(p->seed), p->row_offset, SX, status_word(ws), region(ws, L.c_off), L.part,
+            timing_pair(p, CG_KERNEL_SKETCH), st));
     return from_cuda(launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                               static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
                                               p->row_offset, SX, status_word(ws), static_cast<int>(p->sketch_ctas),
@@ -268,6 +296,7 @@ cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t se
     p->sketch_ctas = 0;
     p->timing = 0;
     p->timing_state = nullptr;
+    p->scatter = 0;
     *out = p;
     return CG_OK;
 }
@@ -331,6 +360,10 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             if (value != 0 && value != 1) return CG_ERR_INVALID_ARG;
             p->timing = static_cast<int32_t>(value);
             return CG_OK;
+        case CG_OPT_SCATTER:
+            if (value < 0 || value > 2) return CG_ERR_INVALID_ARG;
+            p->scatter = static_cast<int32_t>(value);
+            return CG_OK;
         default:
             return CG_ERR_INVALID_ARG;
     }
@@ -345,6 +378,7 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
         case CG_OPT_KSPLIT: *value = p->ksplit; return CG_OK;
         case CG_OPT_SKETCH_CTAS: *value = p->sketch_ctas; return CG_OK;
         case CG_OPT_TIMING: *value = p->timing; return CG_OK;
+        case CG_OPT_SCATTER: *value = p->scatter; return CG_OK;
         default: return CG_ERR_INVALID_ARG;
     }
 }
@@ -377,7 +411,7 @@ cg_status cg_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_i
     if (s != CG_OK) return s;
     Layout L;
     if ((s = check_ws(p, CG_OP_SKETCH, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
-    return run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, as_stream(stream));
+    return run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, L, as_stream(stream));
 }
 
 cg_status cg_sketch_dense(cg_plan *p, const float *X, int64_t ldx, float *SX, void *ws, size_t ws_bytes,
@@ -412,7 +446,7 @@ cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_id
     if ((s = check_ws(p, CG_OP_APPLY_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
     float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
     cudaStream_t st = as_stream(stream);
-    if ((s = run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, st)) != CG_OK) return s;
+    if ((s = run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, L, st)) != CG_OK) return s;
     return run_contract(p, SX, Y, ws, L, st);
 }
 

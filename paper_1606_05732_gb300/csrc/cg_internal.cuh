@@ -21,6 +21,7 @@ struct cg_plan {
     int64_t sketch_ctas;    // 0 = auto
     int32_t timing;         // CG_OPT_TIMING
     void *timing_state;     // cg::TimingState*, created on first timed launch
+    int32_t scatter;        // CG_OPT_SCATTER
 };
 
 namespace cg {
@@ -58,6 +59,23 @@ cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
                                        cudaStream_t stream);
 int sketch_default_ctas();
+
+// ---- partitioned scatter (cg_sketch_part.cu) --------------------------------------
+struct PartLayout {
+    int SB = 0;           // buckets per slice
+    int P = 0;            // slices
+    int G = 0;            // pass-1 CTAs (one record region per CTA and slice)
+    int64_t cap = 0;      // records per region
+    bool det = false;     // exact fixed-point accumulation (deterministic mode)
+    size_t gcount_off = 0, amax_off = 0, rkeys_off = 0, rvals_off = 0, okeys_off = 0, ovals_off = 0;
+    size_t bytes = 0;     // scratch bytes
+};
+bool partition_supported(const cg_plan &p);
+PartLayout partition_layout(const cg_plan &p, int64_t nnz);
+cudaError_t launch_sketch_csr_partitioned(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                          uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                          void *scratch, const PartLayout &L, const EventPair *ev,
+                                          cudaStream_t stream);
 
 // ---- contraction (cg_gauss.cu) ----------------------------------------------
 int contract_splits(const cg_plan &p);

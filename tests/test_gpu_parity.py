@@ -92,10 +92,11 @@ def make_input(n, d, seed, kind):
     return synth.csr_bernoulli(n, d, p, seed=seed, values="uniform" if kind.endswith("u") else "normal")
 
 
+@pytest.mark.parametrize("scatter", ["atomic", "partition"])
 @pytest.mark.parametrize("n,d,m,B,seed,kind", CASES)
-def test_apply_csr_parity(n, d, m, B, seed, kind):
+def test_apply_csr_parity(n, d, m, B, seed, kind, scatter):
     X = make_input(n, d, seed, kind)
-    plan = cg().CountGauss(n, d, m, B, seed)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter=scatter)
     rp, ci, v = dev_csr(X)
     Y = plan.apply_csr(rp, ci, v).cpu().numpy()
     SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
@@ -103,6 +104,51 @@ def test_apply_csr_parity(n, d, m, B, seed, kind):
     Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
     assert rel(SX, SXo) < 1e-6
     assert rel(Y, Yo) < FP32_TOL, rel(Y, Yo)
+
+
+@pytest.mark.parametrize("n,d,m,B,seed,kind", CASES[:4] + [(256, 4096, 8, 512, 9, "bern1.0")])
+def test_deterministic_mode_is_bit_reproducible_and_exact(n, d, m, B, seed, kind):
+    """Deterministic mode sums fixed-point integers (resolution 2^(L+e-62) with
+    2^e > max|x|, 2^L > nnz) and rounds once to fp32: repeated runs are bit-identical,
+    and every SX entry is within one fp32 ulp plus the fixed-point resolution per term
+    of the oracle's FP64 sum; almost all entries equal its fp32 rounding exactly."""
+    X = make_input(n, d, seed, kind)
+    rp, ci, v = dev_csr(X)
+    plan = cg().CountGauss(n, d, m, B, seed, deterministic=True)
+    SX1 = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y1 = plan.apply_csr(rp, ci, v).cpu().numpy()
+    SX2 = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y2 = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    np.testing.assert_array_equal(SX1, SX2)
+    np.testing.assert_array_equal(Y1, Y2)
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    want = SXo.astype(np.float32)
+    L = max(1, int(X.nnz).bit_length())
+    e = int(np.frexp(np.abs(X.vals).max())[1]) if X.nnz else 0
+    per_term = 2.0 ** (L + e - 62)
+    rows_per_bucket = np.bincount(oracle.hash_sign(seed, B, 0, n)[0], minlength=B)
+    bound = np.spacing(np.abs(want)).astype(np.float64) + (rows_per_bucket[:, None] + 1) * per_term
+    assert (np.abs(SX1.astype(np.float64) - SXo) <= bound).all()
+    assert (SX1 == want).mean() > 0.99
+    assert rel(Y1, Yo) < FP32_TOL
+
+
+def test_partition_overflow_path():
+    """Few, full rows of 4096 entries hashed to 64 slices of 8 buckets: some slice
+    receives far more than its share, so its records spill to the overflow list; the
+    result must not change."""
+    n, d, m, B, seed = 256, 4096, 8, 512, 9
+    X = synth.csr_bernoulli(n, d, 1.0, seed=3)
+    rp, ci, v = dev_csr(X)
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    for scatter in ("partition", "atomic"):
+        plan = cg().CountGauss(n, d, m, B, seed, scatter=scatter)
+        SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+        Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+        plan.check()
+        assert rel(SX, SXo) < 1e-6
+        assert rel(Y, Yo) < FP32_TOL
 
 
 @pytest.mark.parametrize("n,d,m,B,seed,kind", CASES)
