@@ -191,6 +191,68 @@ CG_API cg_status cg_sketch_dense(cg_plan *plan, const float *X, int64_t ldx, flo
 CG_API cg_status cg_contract(cg_plan *plan, const float *SX, float *Y,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* ---- many instances in one launch ------------------------------------------------ */
+
+/* One CountGauss instance of a batch: its own plan parameters (as cg_plan_create),
+ * its CSR input (device, conventions as cg_apply_csr) and its output Y (device,
+ * m x d fp32).  Row offset 0, FP32 contraction, atomic scatter. */
+typedef struct cg_batch_desc {
+    int64_t n;
+    int32_t d;
+    int32_t m;
+    int64_t B;
+    uint64_t seed;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const float *vals;
+    int64_t nnz;
+    float *Y;
+} cg_batch_desc;
+
+typedef struct cg_batch_plan cg_batch_plan;
+
+typedef enum cg_batch_option {
+    CG_BATCH_OPT_GRAPH = 1,         /* 1 (default): record the launch once in a CUDA graph and replay it */
+    CG_BATCH_OPT_SCATTER_NNZ = 2,   /* target nonzeros per scatter work item (default 16384) */
+    CG_BATCH_OPT_CONTRACT_FMA = 3,  /* target FMAs per contraction work item (default 2^22) */
+    CG_BATCH_OPT_CTAS_PER_SM = 4,   /* persistent CTAs per SM (default 4) */
+    CG_BATCH_OPT_WAIT_US = 5,       /* bound on a contraction item's wait for its instance's scatter
+                                       (default 2e6 us); on expiry CG_ERR_TIMEOUT via cg_batch_check */
+    CG_BATCH_OPT_TEST_DROP_SCATTER_ITEM = 6 /* test hook: leave the first scatter item of instance 0
+                                               out of the queue, so that its wait runs out */
+} cg_batch_option;
+
+/* Plan a batch (host only; copies the descriptors).  The work of every instance is cut
+ * into scatter items (rows) and contraction items (K slabs); one persistent kernel
+ * claims them in order, and an instance's contraction items wait (bounded) for its
+ * scatter items.  The plan keeps the pointers in the descriptors: the buffers they
+ * name must stay valid while the plan is used. */
+CG_API cg_status cg_batch_plan_create(const cg_batch_desc *descs, int32_t count, cg_batch_plan **out);
+CG_API cg_status cg_batch_plan_destroy(cg_batch_plan *plan);
+CG_API cg_status cg_batch_set_option(cg_batch_plan *plan, int32_t option, int64_t value);
+CG_API cg_status cg_batch_plan_get_option(const cg_batch_plan *plan, int32_t option, int64_t *value);
+
+/* Device workspace for cg_batch_apply (first 256 bytes: status word, zeroed once by
+ * the caller as for cg_apply_csr). */
+CG_API cg_status cg_batch_workspace_size(const cg_batch_plan *plan, size_t *bytes);
+
+/* Run every instance: Y_k = G_k.(S_k.X_k).  The first call with a given workspace
+ * uploads the instance table and work queue (a host-to-device copy) and, with
+ * CG_BATCH_OPT_GRAPH, records the memset and the persistent launch in a CUDA graph;
+ * later calls with the same workspace replay the graph on `stream`.  Read the status
+ * word with cg_batch_check. */
+CG_API cg_status cg_batch_apply(cg_batch_plan *plan, void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronise `stream`, read and clear the status word of a batch workspace:
+ * CG_OK, CG_ERR_TIMEOUT or CG_ERR_DEVICE_BOUNDS. */
+CG_API cg_status cg_batch_check(const cg_batch_plan *plan, void *ws, void *stream);
+
+/* Autotuner: times the batch `reps` times for each of a small grid of work-item sizes
+ * and CTAs per SM (synchronises), keeps the fastest in the plan and returns its time
+ * per run in *best_ms (may be NULL). */
+CG_API cg_status cg_batch_autotune(cg_batch_plan *plan, void *ws, size_t ws_bytes, void *stream, int32_t reps,
+                                   double *best_ms);
+
 /* ---- without a workspace ------------------------------------------------------ */
 
 /* The paper has no counterpart to this entry point; it exists for callers that

@@ -47,10 +47,29 @@ SIGNATURES = {
     "cg_sketch_csr": [P, P, P, P, I64, P, P, SZ, P],
     "cg_sketch_dense": [P, P, I64, P, P, SZ, P],
     "cg_contract": [P, P, P, P, SZ, P],
+    "cg_batch_plan_create": [P, I32, ctypes.POINTER(P)],
+    "cg_batch_plan_destroy": [P],
+    "cg_batch_set_option": [P, I32, I64],
+    "cg_batch_plan_get_option": [P, I32, ctypes.POINTER(I64)],
+    "cg_batch_workspace_size": [P, ctypes.POINTER(SZ)],
+    "cg_batch_apply": [P, P, SZ, P],
+    "cg_batch_check": [P, P, P],
+    "cg_batch_autotune": [P, P, SZ, P, I32, ctypes.POINTER(ctypes.c_double)],
     "cg_generate_words": [U64, U32, U64, I64, P, P],
     "cg_generate_hash_sign": [U64, I64, I64, I64, P, P, P],
     "cg_generate_gaussian": [U64, U32, I64, I64, I64, I64, I64, P, P],
 }
+
+
+BATCH_OPT_GRAPH, BATCH_OPT_SCATTER_NNZ, BATCH_OPT_CONTRACT_FMA, BATCH_OPT_CTAS_PER_SM = 1, 2, 3, 4
+BATCH_OPT_WAIT_US, BATCH_OPT_TEST_DROP_SCATTER_ITEM = 5, 6
+
+
+class BatchDesc(ctypes.Structure):
+    """cg_batch_desc."""
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("m", ctypes.c_int32), ("B", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("nnz", ctypes.c_int64), ("Y", ctypes.c_void_p)]
 
 
 class CountGaussError(RuntimeError):

@@ -194,6 +194,80 @@ class CountGauss:
         return Y
 
 
+# -- batches -----------------------------------------------------------------------
+class CountGaussBatch:
+    """Many instances in one persistent launch (cg_batch_plan_create / cg_batch_apply).
+
+    `instances` is a list of dicts with keys n, d, m, B, seed, row_ptr, col_idx, vals
+    (CUDA tensors: int32, int32, float32).  Outputs are allocated here (self.Y[k], m x d);
+    the tensors are kept alive by this object, since the plan holds their pointers."""
+
+    def __init__(self, instances, *, graph: bool = True, wait_us: int | None = None):
+        lib = _lib.load()
+        self._lib = lib
+        self._keep = []
+        self.Y = []
+        descs = (_lib.BatchDesc * len(instances))()
+        dev = None
+        for k, inst in enumerate(instances):
+            rp = _need(inst["row_ptr"], torch.int32, "row_ptr")
+            ci = _need(inst["col_idx"], torch.int32, "col_idx")
+            v = _need(inst["vals"], torch.float32, "vals")
+            dev = rp.device
+            Y = torch.empty(inst["m"], inst["d"], dtype=torch.float32, device=dev)
+            self._keep += [rp, ci, v]
+            self.Y.append(Y)
+            descs[k] = _lib.BatchDesc(inst["n"], inst["d"], inst["m"], inst["B"], inst["seed"], rp.data_ptr(),
+                                      ci.data_ptr(), v.data_ptr(), ci.numel(), Y.data_ptr())
+        self.device = dev if dev is not None else torch.device("cuda")
+        h = _P()
+        _lib.check("cg_batch_plan_create",
+                   lib.cg_batch_plan_create(ctypes.cast(descs, _P), len(instances), ctypes.byref(h)))
+        self._h = h
+        self.set_option(_lib.BATCH_OPT_GRAPH, int(bool(graph)))
+        if wait_us is not None:
+            self.set_option(_lib.BATCH_OPT_WAIT_US, int(wait_us))
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.cg_batch_plan_destroy(h)
+            self._h = None
+
+    def set_option(self, option: int, value: int) -> None:
+        _lib.check("cg_batch_set_option", self._lib.cg_batch_set_option(self._h, option, int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int64()
+        _lib.check("cg_batch_plan_get_option", self._lib.cg_batch_plan_get_option(self._h, option, ctypes.byref(v)))
+        return int(v.value)
+
+    def workspace(self) -> torch.Tensor:
+        sz = ctypes.c_size_t()
+        _lib.check("cg_batch_workspace_size", self._lib.cg_batch_workspace_size(self._h, ctypes.byref(sz)))
+        if self._ws is None or self._ws.numel() < sz.value:
+            self._ws = torch.empty(max(int(sz.value), 256), dtype=torch.uint8, device=self.device)
+            self._ws[:256].zero_()
+        return self._ws
+
+    def apply(self):
+        ws = self.workspace()
+        _lib.check("cg_batch_apply", self._lib.cg_batch_apply(self._h, _ptr(ws), ws.numel(), _stream(self.device)))
+        return self.Y
+
+    def check(self) -> None:
+        ws = self.workspace()
+        _lib.check("cg_batch_check", self._lib.cg_batch_check(self._h, _ptr(ws), _stream(self.device)))
+
+    def autotune(self, reps: int = 3) -> float:
+        ws = self.workspace()
+        best = ctypes.c_double()
+        _lib.check("cg_batch_autotune", self._lib.cg_batch_autotune(self._h, _ptr(ws), ws.numel(),
+                                                                    _stream(self.device), reps, ctypes.byref(best)))
+        return float(best.value)
+
+
 # -- generator dumps (bit-exact checks against the oracle) -----------------------
 def generate_words(seed: int, tag: int, idx0: int, count: int, device="cuda") -> torch.Tensor:
     out = torch.empty(count, 4, dtype=torch.int32, device=device)

@@ -13,6 +13,7 @@
 // bit-reproducible for a given grid.
 #include <algorithm>
 
+#include "cg_ffma.cuh"
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -27,128 +28,12 @@ template <int TN>
 __global__ void __launch_bounds__(kThreads)
 contract_ffma_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_split,
                      bool vec_x, float *__restrict__ part) {
-    constexpr int BN = 16 * TN;
-    constexpr int kMainFloats = kKT * (kBM + BN);
-    constexpr int kRedFloats = kThreads * 4 * TN;
-    constexpr int kRawFloats = kMainFloats > kRedFloats ? kMainFloats : kRedFloats;
-    __shared__ __align__(16) float raw[kRawFloats];
-    float(*sG)[kBM] = reinterpret_cast<float(*)[kBM]>(raw);                // [kKT][kBM]
-    float(*sX)[BN] = reinterpret_cast<float(*)[BN]>(raw + kKT * kBM);      // [kKT][BN]
-
-    const int split = blockIdx.x;
-    const int m0 = blockIdx.y * kBM;
-    const int n0 = blockIdx.z * BN;
-    const int bm = min(kBM, m - m0);
-    const int bn = min(BN, d - n0);
-    const int mt = (bm + 3) >> 2;
-    const int nt = (bn + TN - 1) / TN;
-    const int tiles = mt * nt;
-    const int kg = max(1, kThreads / tiles);
-    const int t = threadIdx.x;
-    const int tile = t % tiles;
-    const int grp = t / tiles;
-    const bool active = grp < kg;
-    const int ti = tile % mt;
-    const int tj = tile / mt;
-    const uint64_t groups = static_cast<uint64_t>((m + 3) >> 2);
-    const int g0 = m0 >> 2;
-
-    float acc[4][TN];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
-
+    __shared__ __align__(16) float raw[FfmaShape<TN>::kRawFloats];
     const int64_t nslabs = (B + kKT - 1) / kKT;
-    const int64_t s_begin = static_cast<int64_t>(split) * slabs_per_split;
+    const int64_t s_begin = static_cast<int64_t>(blockIdx.x) * slabs_per_split;
     const int64_t s_end = min(nslabs, s_begin + slabs_per_split);
-
-    for (int64_t sl = s_begin; sl < s_end; ++sl) {
-        const int64_t b0 = sl * kKT;
-        // G[m0 .. m0+4mt, b0 .. b0+kKT): quads of four rows of one column.
-        for (int q = t; q < mt * kKT; q += kThreads) {
-            const int gl = q % mt;
-            const int kk = q / mt;
-            const int64_t b = b0 + kk;
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (b < B) z = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(b), static_cast<uint64_t>(g0 + gl));
-            *reinterpret_cast<float4 *>(&sG[kk][4 * gl]) = z;
-        }
-        // SX[b0 .. b0+kKT, n0 .. n0+bn)
-        if (vec_x) {
-            constexpr int BQ = BN / 4;
-            for (int q = t; q < kKT * BQ; q += kThreads) {
-                const int kk = q / BQ;
-                const int cq = q % BQ;
-                const int64_t b = b0 + kk;
-                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (b < B && 4 * cq < bn) x = __ldg(reinterpret_cast<const float4 *>(SX + b * d + n0) + cq);
-                *reinterpret_cast<float4 *>(&sX[kk][4 * cq]) = x;
-            }
-        } else {
-            for (int q = t; q < kKT * BN; q += kThreads) {
-                const int kk = q / BN;
-                const int cc = q % BN;
-                const int64_t b = b0 + kk;
-                sX[kk][cc] = (b < B && cc < bn) ? __ldg(SX + b * d + n0 + cc) : 0.0f;
-            }
-        }
-        __syncthreads();
-        if (active) {
-            for (int kk = grp; kk < kKT; kk += kg) {
-                const float4 a = *reinterpret_cast<const float4 *>(&sG[kk][4 * ti]);
-                float bv[TN];
-#pragma unroll
-                for (int j4 = 0; j4 < TN / 4; ++j4) {
-                    const float4 x = *reinterpret_cast<const float4 *>(&sX[kk][TN * tj + 4 * j4]);
-                    bv[4 * j4 + 0] = x.x;
-                    bv[4 * j4 + 1] = x.y;
-                    bv[4 * j4 + 2] = x.z;
-                    bv[4 * j4 + 3] = x.w;
-                }
-#pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    acc[0][j] = fmaf(a.x, bv[j], acc[0][j]);
-                    acc[1][j] = fmaf(a.y, bv[j], acc[1][j]);
-                    acc[2][j] = fmaf(a.z, bv[j], acc[2][j]);
-                    acc[3][j] = fmaf(a.w, bv[j], acc[3][j]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-
-    // Sum the k-groups in a fixed order (group 0 + group 1 + ...).
-    if (kg > 1) {
-        float *red = raw;
-        if (active && grp > 0) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < TN; ++j) red[((grp - 1) * tiles + tile) * 4 * TN + i * TN + j] = acc[i][j];
-        }
-        __syncthreads();
-        if (grp == 0) {
-            for (int g = 1; g < kg; ++g)
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) acc[i][j] += red[((g - 1) * tiles + tile) * 4 * TN + i * TN + j];
-        }
-    }
-    if (grp == 0) {
-        float *out = part + static_cast<size_t>(split) * m * d;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = m0 + 4 * ti + i;
-            if (r >= m) continue;
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const int c = n0 + TN * tj + j;
-                if (TN * tj + j < bn) out[static_cast<size_t>(r) * d + c] = acc[i][j];
-            }
-        }
-    }
+    ffma_block<TN, false>(SX, m, d, B, key, s_begin, s_end, blockIdx.y * kBM, blockIdx.z * 16 * TN, vec_x,
+                          part + static_cast<size_t>(blockIdx.x) * m * d, raw);
 }
 
 // Y[o] = sum over s of part[s][o], s in increasing order within each of 8 lanes,

@@ -8,6 +8,7 @@
 // bucket and sign of a row are recomputed from the Philox stream by the lane that
 // owns the row and shared through shared memory; nothing random is stored.
 #include "cg_internal.cuh"
+#include "cg_scatter.cuh"
 
 namespace cg {
 
@@ -17,10 +18,9 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kUnroll = 4;  // nonzeros in flight per lane
 
-// One warp owns a chunk of 32 consecutive rows at a time.  Lane l hashes row l of
-// the chunk and loads its row_ptr entry; the chunk's nonzeros [beg, end) are then
-// swept 32 x kUnroll at a time with coalesced loads, and each nonzero finds its
-// row by a 5-step binary search over the chunk's 33 row offsets in shared memory.
+// One warp owns a chunk of 32 consecutive rows at a time (scatter_chunk32): lane l
+// hashes row l of the chunk, the chunk's nonzeros are swept with coalesced loads and
+// each becomes one fp32 reduction into SX.
 __global__ void __launch_bounds__(kThreads)
 sketch_csr_atomic_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                          const float *__restrict__ vals, int n, int d, uint32_t B, int nnz, Key key,
@@ -28,64 +28,12 @@ sketch_csr_atomic_kernel(const int *__restrict__ row_ptr, const int *__restrict_
     __shared__ int s_rp[kWarps][33];
     __shared__ uint32_t s_h[kWarps][32];
     __shared__ float s_sg[kWarps][32];
-    const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int nchunks = (n + 31) >> 5;
     int bad = 0;
-    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
-        const int first = c << 5;
-        const int i = first + lane;
-        const int last = min(first + 32, n);
-        const int end = __ldg(row_ptr + last);
-        int rp = end;
-        uint32_t h = 0;
-        float sg = 0.0f;
-        if (i < n) {
-            rp = __ldg(row_ptr + i);
-            hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
-        }
-        s_rp[w][lane] = rp;
-        s_h[w][lane] = h;
-        s_sg[w][lane] = sg;
-        if (lane == 0) s_rp[w][32] = end;
-        __syncwarp();
-        const int beg = s_rp[w][0];
-        if (beg < 0 || end > nnz || beg > end) {  // malformed row_ptr: skip the chunk
-            bad = 1;
-            __syncwarp();
-            continue;
-        }
-        for (int k0 = beg; k0 < end; k0 += 32 * kUnroll) {
-            int col[kUnroll];
-            float v[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int k = k0 + u * 32 + lane;
-                col[u] = -1;
-                v[u] = 0.0f;
-                if (k < end) {
-                    col[u] = __ldg(col_idx + k);
-                    v[u] = __ldg(vals + k);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int k = k0 + u * 32 + lane;
-                if (k < end) {
-                    int lo = 0;
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (s_rp[w][lo + step] <= k) lo += step;
-                    const int j = col[u];
-                    if (static_cast<unsigned>(j) < static_cast<unsigned>(d))
-                        atomicAdd(SX + static_cast<size_t>(s_h[w][lo]) * d + j, s_sg[w][lo] * v[u]);
-                    else
-                        bad = 1;
-                }
-            }
-        }
-        __syncwarp();
-    }
+    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps)
+        scatter_chunk32(row_ptr, col_idx, vals, c << 5, n, d, B, nnz, key, row_offset, SX, s_rp[w], s_h[w], s_sg[w],
+                        bad);
     if (bad) atomicOr(status, kStatusBounds);
 }
 

@@ -73,3 +73,24 @@ def test_fullsize_precision_ladder(ladder_case, precision, bound):
     err = rel(Y, Yo)
     print(f"ladder_n64M_d128 {precision}: rel Frobenius error {err:.3e} (bound {bound})")
     assert err < bound
+
+
+def test_fullsize_batch_96_instances():
+    """The 96-instance batch (seeds 100..195), autotuned, every output against the oracle."""
+    from paper_1606_05732_gb300 import countgauss
+    params = synth.batch_instances()
+    Xs = synth.batch_inputs(params)
+    insts = [dict(n=t.n, d=t.d, m=t.m, B=t.B, seed=t.seed,
+                  row_ptr=torch.from_numpy(X.row_ptr.astype(np.int32)).cuda(),
+                  col_idx=torch.from_numpy(X.col_idx).cuda(), vals=torch.from_numpy(X.vals).cuda())
+             for t, X in zip(params, Xs)]
+    batch = countgauss.CountGaussBatch(insts)
+    batch.autotune(reps=2)
+    Ys = [y.cpu().numpy() for y in batch.apply()]
+    batch.check()
+    worst = 0.0
+    for t, X, Y in zip(params, Xs, Ys):
+        Yo = oracle.apply_csr(t.seed, t.n, t.d, t.m, t.B, X.row_ptr, X.col_idx, X.vals)
+        worst = max(worst, rel(Y, Yo))
+    print(f"batch of 96: worst rel Frobenius error {worst:.3e}")
+    assert worst < FP32_TOL
