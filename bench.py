@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scatter", choices=["auto", "atomic", "partition"], default="auto")
+    ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
     return ap.parse_args()
 
 
@@ -200,6 +201,104 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------
+def _time_calls(fn, reps, stream, warm=2):
+    """Mean ms per call of fn over `reps` calls, CUDA events on `stream`."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_rows(dev, reps):
+    """The other rows of the hot path, each on its own workload (sizes in synth.WORKLOADS):
+    precision ladder and plain product on the largest workload, dense forward and
+    adjoint, the 96-instance batch, deterministic mode, and the small case's latency."""
+    import numpy as np
+    import torch
+
+    from paper_1606_05732_gb300 import _lib, countgauss, synth
+
+    stream = torch.cuda.current_stream(dev)
+    rows = {}
+
+    def csr_dev(X):
+        return (torch.from_numpy(X.row_ptr.astype(np.int32)).to(dev), torch.from_numpy(X.col_idx).to(dev),
+                torch.from_numpy(X.vals).to(dev))
+
+    # precision ladder + plain product at the largest workload
+    X, w = synth.workload_csr("ladder_n64M_d128")
+    rp, ci, v = csr_dev(X)
+    ladder = {}
+    for prec in ["fp32", "bf16x3", "bf16", "fp8x3", "fp8"]:
+        plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"], precision=prec)
+        Y = torch.empty(w["m"], w["d"], dtype=torch.float32, device=dev)
+        plan.apply_csr(rp, ci, v, out=Y)
+        plan.enable_timing(True)
+        plan.kernel_time(_lib.KERNEL_CONTRACT)
+        ms = _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, stream)
+        cms, cn = plan.kernel_time(_lib.KERNEL_CONTRACT)
+        plan.check()
+        flops = 2.0 * w["m"] * w["B"] * w["d"]
+        ladder[prec] = {"ms_per_call": ms, "nnz_per_s": X.nnz / (ms / 1e3), "contract_kernel_ms": cms / max(1, cn),
+                        "contract_tflops": flops / (cms / max(1, cn) / 1e3) / 1e12}
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"])
+    Yp = torch.empty(w["m"], w["d"], dtype=torch.float32, device=dev)
+    plain_ms = _time_calls(lambda: plan.plain_csr(rp, ci, v, out=Yp), max(2, reps // 4), stream, warm=1)
+    rows["ladder_n64M_d128"] = {"nnz": X.nnz, "m": w["m"], "B": w["B"], "d": w["d"], "precisions": ladder,
+                                "plain_ms": plain_ms,
+                                "speedup_fp32_over_plain": plain_ms / ladder["fp32"]["ms_per_call"]}
+    del rp, ci, v, X
+
+    # dense forward and adjoint (dense and at the stored entries of the p = 0.02 variant)
+    w = synth.WORKLOADS["grad_n1M_d64"]
+    Xd = torch.from_numpy(synth.dense_normal(w["n"], w["d"], seed=w["seed"])).to(dev)
+    Xs = synth.csr_bernoulli(w["n"], w["d"], w["p"], seed=w["seed"])
+    rp, ci, v = csr_dev(Xs)
+    plan = countgauss.CountGauss(w["n"], w["d"], w["m"], w["B"], w["seed"])
+    dY = torch.randn(w["m"], w["d"], device=dev)
+    fwd = _time_calls(lambda: plan.apply_dense(Xd), reps, stream)
+    bwd = _time_calls(lambda: plan.adjoint(dY), reps, stream)
+    bwd_s = _time_calls(lambda: plan.adjoint(dY, rp, ci), reps, stream)
+    dense_bytes = 4 * w["n"] * w["d"]
+    rows["grad_n1M_d64"] = {"apply_dense_ms": fwd, "apply_dense_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / fwd / 1e6,
+                            "adjoint_dense_ms": bwd, "adjoint_dense_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / bwd / 1e6,
+                            "adjoint_csr_ms": bwd_s, "adjoint_csr_nnz": Xs.nnz}
+    del Xd, rp, ci, v
+
+    # the 96-instance batch, autotuned, replayed from a CUDA graph
+    params = synth.batch_instances()
+    Xs = synth.batch_inputs(params)
+    insts = []
+    for t, Xb in zip(params, Xs):
+        rpb, cib, vb = csr_dev(Xb)
+        insts.append(dict(n=t.n, d=t.d, m=t.m, B=t.B, seed=t.seed, row_ptr=rpb, col_idx=cib, vals=vb))
+    batch = countgauss.CountGaussBatch(insts)
+    batch.autotune(reps=2)
+    bms = _time_calls(batch.apply, reps, stream)
+    batch.check()
+    tot = sum(X.nnz for X in Xs)
+    rows["batch96"] = {"ms_per_batch": bms, "nnz_total": tot, "nnz_per_s": tot / (bms / 1e3),
+                       "tuning": {"scatter_nnz": batch.get_option(_lib.BATCH_OPT_SCATTER_NNZ),
+                                  "contract_fma": batch.get_option(_lib.BATCH_OPT_CONTRACT_FMA),
+                                  "ctas_per_sm": batch.get_option(_lib.BATCH_OPT_CTAS_PER_SM)}}
+    del insts, batch
+
+    # small case latency
+    X, w = synth.workload_csr("small_n65536_d16")
+    rp, ci, v = csr_dev(X)
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"])
+    rows["small_n65536_d16"] = {"apply_csr_us": 1e3 * _time_calls(lambda: plan.apply_csr(rp, ci, v), reps, stream),
+                                "plain_us": 1e3 * _time_calls(lambda: plan.plain_csr(rp, ci, v), reps, stream)}
+    return rows
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -224,7 +323,7 @@ def run_ours(args):
     v_h = torch.from_numpy(X.vals).pin_memory()
     rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
     plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter)
-    partitioned = args.scatter != "atomic"  # auto picks the partitioned scatter for this workload
+    partitioned = args.scatter == "partition"  # auto: the atomic scatter
     scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_atomic_kernel")
     scatter_src = ("cg_sketch_part.cu", "cg_rng.cuh") if partitioned else ("cg_sketch.cu", "cg_rng.cuh")
     Y = torch.empty(m, d, dtype=torch.float32, device=dev)
@@ -288,6 +387,13 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     plain_ms = p0.elapsed_time(p1) / plain_steps
 
+    # deterministic mode (bucket-range partition + exact fixed-point sums) on the same input
+    det_plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, deterministic=True)
+    Yd = torch.empty_like(Y)
+    det_ms = _time_calls(lambda: det_plan.apply_csr(rp, ci, v, out=Yd), max(3, args.steps // 10), stream)
+    det_plan.check()
+    del det_plan
+
     # end to end through the same call: H2D of the CSR, apply, D2H of Y, every step
     rp2, ci2, v2 = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(v)
     Y_h = torch.empty(m, d, dtype=torch.float32).pin_memory()
@@ -318,6 +424,12 @@ def run_ours(args):
         e2e_ms = float(t.item())
     h2d = int(rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 4)
     d2h = int(m * d * 4)
+
+    rows = None
+    if rank == 0 and world == 1 and not args.no_rows:
+        del rp2, ci2, v2
+        torch.cuda.empty_cache()
+        rows = measure_rows(dev, max(5, args.steps // 10))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -354,6 +466,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(),
+            "deterministic": {"ms_per_step": det_ms, "value": world * nnz / (det_ms / 1e3), "unit": UNIT},
+            "rows": rows,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -153,12 +153,22 @@ bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t
 
 cg_status from_cuda(cudaError_t e) { return e == cudaSuccess ? CG_OK : CG_ERR_CUDA; }
 
-// Whether a CSR scatter through plan p uses the partitioned algorithm: always in
-// deterministic mode (exact fixed-point accumulation), on request otherwise (the
-// default atomic scatter is faster at present).
+// Whether a CSR scatter through plan p uses the partitioned algorithm (on request
+// only: the atomic scatter is faster at present).  Deterministic mode uses the
+// fixed-point scatter instead.
 bool use_partition(const cg_plan &p) {
-    if (p.deterministic) return partition_supported(p);
+    if (p.deterministic) return false;
     return p.scatter == 2 && partition_supported(p);
+}
+
+// Scratch bytes of the CSR scatter through plan p (region C).
+size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
+    if (p.deterministic) return sketch_fixed_scratch_bytes(p.B, p.d);
+    if (use_partition(p)) {
+        *part = partition_layout(p, nnz);
+        return part->bytes;
+    }
+    return 0;
 }
 
 // Workspace layout: [status 256 B][region A][region B][region C], each 256-aligned.
@@ -178,10 +188,7 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
         case CG_OP_APPLY_CSR:
             L.a_bytes = sx;
             L.b_bytes = contract_partials_bytes(p);
-            if (use_partition(p)) {
-                L.part = partition_layout(p, nnz);
-                L.c_bytes = L.part.bytes;
-            }
+            L.c_bytes = scatter_scratch(p, nnz, &L.part);
             break;
         case CG_OP_APPLY_DENSE:
             L.a_bytes = sx;
@@ -198,10 +205,7 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
             L.b_bytes = static_cast<size_t>(plain_ctas(p.m, p.d)) * p.m * p.d * sizeof(float);
             break;
         case CG_OP_SKETCH:
-            if (use_partition(p)) {
-                L.part = partition_layout(p, nnz);
-                L.c_bytes = L.part.bytes;
-            }
+            L.c_bytes = scatter_scratch(p, nnz, &L.part);
             break;
         default:
             break;
@@ -246,7 +250,11 @@ cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const La
 
 cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                          int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st) {
-    if (p->deterministic && !use_partition(*p)) return CG_ERR_UNSUPPORTED;
+    if (p->deterministic)
+        return from_cuda(launch_sketch_csr_fixed(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
+                                                 static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
+                                                 p->row_offset, SX, region(ws, L.c_off), status_word(ws),
+                                                 static_cast<int>(p->sketch_ctas), timing_pair(p, CG_KERNEL_SKETCH), st));
     if (use_partition(*p))
         return from_cuda(launch_sketch_csr_partitioned(
             row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), static_cast<int>(nnz),

@@ -83,7 +83,7 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
         const BatchInst I = insts[item.inst];
         if (item.kind == 0) {
             for (int first = item.a + w * 32; first < item.b; first += kBWarps * 32)
-                scatter_chunk32(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, I.key, 0, I.SX, s_rp[w],
+                scatter_chunk32<false>(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, I.key, 0, I.SX, 0, s_rp[w],
                                 s_h[w], s_sg[w], bad);
             __syncthreads();
             if (t == 0) {

@@ -59,6 +59,11 @@ cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
                                        cudaStream_t stream);
 int sketch_default_ctas();
+// Deterministic scatter: exact int64 fixed-point sums (scratch of sketch_fixed_scratch_bytes).
+size_t sketch_fixed_scratch_bytes(int64_t B, int d);
+cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                    uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, void *scratch,
+                                    int *status, int ctas, const EventPair *ev, cudaStream_t stream);
 
 // ---- partitioned scatter (cg_sketch_part.cu) --------------------------------------
 struct PartLayout {
@@ -66,7 +71,6 @@ struct PartLayout {
     int P = 0;            // slices
     int G = 0;            // pass-1 CTAs (one record region per CTA and slice)
     int64_t cap = 0;      // records per region
-    bool det = false;     // exact fixed-point accumulation (deterministic mode)
     size_t gcount_off = 0, amax_off = 0, rkeys_off = 0, rvals_off = 0, okeys_off = 0, ovals_off = 0;
     size_t bytes = 0;     // scratch bytes
 };

@@ -36,10 +36,11 @@ __host__ __device__ __forceinline__ Key make_key(uint64_t seed) {
 __device__ __forceinline__ uint4 philox10(uint4 c, Key k) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t a = c.x, b = c.z;
-        const uint32_t hi_a = __umulhi(0xD2511F53u, a), lo_a = 0xD2511F53u * a;
-        const uint32_t hi_b = __umulhi(0xCD9E8D57u, b), lo_b = 0xCD9E8D57u * b;
-        c = make_uint4(hi_b ^ c.y ^ k.k0, lo_b, hi_a ^ c.w ^ k.k1, lo_a);
+        // one 32x32->64 product per multiplier: high and low halves from the same product
+        const uint64_t pa = static_cast<uint64_t>(0xD2511F53u) * c.x;
+        const uint64_t pb = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+        c = make_uint4(static_cast<uint32_t>(pb >> 32) ^ c.y ^ k.k0, static_cast<uint32_t>(pb),
+                       static_cast<uint32_t>(pa >> 32) ^ c.w ^ k.k1, static_cast<uint32_t>(pa));
         k.k0 += 0x9E3779B9u;
         k.k1 += 0xBB67AE85u;
     }

@@ -7,17 +7,69 @@ namespace cg {
 
 constexpr int kScatterUnroll = 4;  // nonzeros in flight per lane
 
+// L2 policy for data read exactly once (the CSR stream): evict it first, so that it
+// does not push the sketch SX, which is reduced into over and over, out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ int ld_stream_i32(const int *p, uint64_t pol) {
+    int v;
+    asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ float ld_stream_f32(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Scale of the fixed-point sums: F = 62 - L - e with max|x| < 2^e and nnz < 2^L, so
+// every term is below 2^(62-L) and no sum of nnz terms leaves the int64 range.  Each
+// term is resolved to 2^-F = 2^(L+e-62) absolute (about 1e-11 of max|x| at nnz ~ 5e7).
+__device__ __forceinline__ int fixed_point_exponent(int maxbits, int nnz) {
+    const float mx = __int_as_float(maxbits);
+    int e = 0;
+    if (mx > 0.0f) frexpf(mx, &e);  // mx < 2^e
+    const int L = nnz > 0 ? 32 - __clz(nnz) : 1;  // nnz < 2^L
+    return 62 - L - e;
+}
+
+// Fixed-point image of v: round(v 2^F) as a two's-complement 64-bit integer, with
+// integer operations only.  The caller picks F so that |v| 2^F < 2^62.
+__device__ __forceinline__ unsigned long long to_fixed(float v, int F) {
+    const uint32_t u = __float_as_uint(v);
+    const int be = static_cast<int>((u >> 23) & 0xFFu);
+    if (be == 0xFF) return 0ull;  // not finite: contributes nothing
+    const uint32_t mant = (u & 0x7FFFFFu) | (be ? 0x800000u : 0u);
+    const int sh = (be ? be : 1) - 150 + F;  // |v| = mant 2^(exp - 150), times 2^F
+    long long q;
+    if (sh >= 0)
+        q = static_cast<long long>(mant) << (sh < 39 ? sh : 39);
+    else if (sh > -25)
+        q = static_cast<long long>((mant + (1u << (-sh - 1))) >> (-sh));  // round half up
+    else
+        q = 0;
+    return static_cast<unsigned long long>((u >> 31) ? -q : q);
+}
+
 // Rows [first, min(first + 32, n)) of a CSR matrix: lane l hashes row first + l and
 // loads its row_ptr entry into the warp's shared arrays s_rp[33], s_h[32], s_sg[32];
 // the rows' nonzeros [beg, end) are swept 32 x kScatterUnroll at a time with coalesced
-// loads, each nonzero finds its row by a 5-step binary search over s_rp and becomes
-// one fp32 reduction SX[h, j] += sigma x.  Out-of-range column indices and malformed
-// row offsets are skipped and reported through `bad`.
+// evict-first loads, each nonzero finds its row by a 5-step binary search over s_rp and
+// becomes one reduction into SX: fp32, or with FIXED the 64-bit integer to_fixed(x, F)
+// into an integer SX (order-independent sums).  Out-of-range column indices and
+// malformed row offsets are skipped and reported through `bad`.
+template <bool FIXED>
 __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                                 const float *__restrict__ vals, int first, int n, int d, uint32_t B,
-                                                int nnz, Key key, int64_t row_offset, float *__restrict__ SX,
+                                                int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
                                                 int *s_rp, uint32_t *s_h, float *s_sg, int &bad) {
     const int lane = threadIdx.x & 31;
+    const uint64_t pol = l2_evict_first_policy();
     const int i = first + lane;
     const int last = min(first + 32, n);
     const int end = __ldg(row_ptr + last);
@@ -25,7 +77,7 @@ __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr,
     uint32_t h = 0;
     float sg = 0.0f;
     if (i < n) {
-        rp = __ldg(row_ptr + i);
+        rp = ld_stream_i32(row_ptr + i, pol);
         hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
     }
     s_rp[lane] = rp;
@@ -48,8 +100,8 @@ __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr,
             col[u] = -1;
             v[u] = 0.0f;
             if (k < end) {
-                col[u] = __ldg(col_idx + k);
-                v[u] = __ldg(vals + k);
+                col[u] = ld_stream_i32(col_idx + k, pol);
+                v[u] = ld_stream_f32(vals + k, pol);
             }
         }
 #pragma unroll
@@ -61,10 +113,15 @@ __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr,
                 for (int step = 16; step > 0; step >>= 1)
                     if (s_rp[lo + step] <= k) lo += step;
                 const int j = col[u];
-                if (static_cast<unsigned>(j) < static_cast<unsigned>(d))
-                    atomicAdd(SX + static_cast<size_t>(s_h[lo]) * d + j, s_sg[lo] * v[u]);
-                else
+                if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
+                    const size_t at = static_cast<size_t>(s_h[lo]) * d + j;
+                    if (FIXED)
+                        atomicAdd(static_cast<unsigned long long *>(SX) + at, to_fixed(s_sg[lo] * v[u], F));
+                    else
+                        atomicAdd(static_cast<float *>(SX) + at, s_sg[lo] * v[u]);
+                } else {
                     bad = 1;
+                }
             }
         }
     }

@@ -20,21 +20,48 @@ constexpr int kUnroll = 4;  // nonzeros in flight per lane
 
 // One warp owns a chunk of 32 consecutive rows at a time (scatter_chunk32): lane l
 // hashes row l of the chunk, the chunk's nonzeros are swept with coalesced loads and
-// each becomes one fp32 reduction into SX.
+// each becomes one reduction into SX (fp32; with FIXED, int64 fixed point).
+template <bool FIXED>
 __global__ void __launch_bounds__(kThreads)
-sketch_csr_atomic_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
-                         const float *__restrict__ vals, int n, int d, uint32_t B, int nnz, Key key,
-                         int64_t row_offset, float *__restrict__ SX, int *__restrict__ status) {
+sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
+                  int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *__restrict__ SX,
+                  const int *__restrict__ maxbits, int *__restrict__ status) {
     __shared__ int s_rp[kWarps][33];
     __shared__ uint32_t s_h[kWarps][32];
     __shared__ float s_sg[kWarps][32];
     const int w = threadIdx.x >> 5;
     const int nchunks = (n + 31) >> 5;
+    const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
     int bad = 0;
     for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps)
-        scatter_chunk32(row_ptr, col_idx, vals, c << 5, n, d, B, nnz, key, row_offset, SX, s_rp[w], s_h[w], s_sg[w],
-                        bad);
+        scatter_chunk32<FIXED>(row_ptr, col_idx, vals, c << 5, n, d, B, nnz, key, row_offset, SX, F, s_rp[w], s_h[w],
+                               s_sg[w], bad);
     if (bad) atomicOr(status, kStatusBounds);
+}
+
+// max |x| over the stored values, as the bit pattern of a non-negative float (whose
+// integer order is its numeric order) combined with atomicMax.
+__global__ void __launch_bounds__(kThreads)
+absmax_kernel(const float *__restrict__ x, int64_t count, int *__restrict__ maxbits) {
+    float mx = 0.0f;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * kThreads) {
+        const float a = fabsf(__ldg(x + i));
+        if (a <= 3.0e38f) mx = fmaxf(mx, a);  // finite values only
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0f) atomicMax(maxbits, __float_as_int(mx));
+}
+
+// SX = (float)(acc 2^-F): one rounding of the exact fixed-point sums.
+__global__ void __launch_bounds__(kThreads)
+fixed_to_float_kernel(const unsigned long long *__restrict__ acc, int64_t count, const int *__restrict__ maxbits,
+                      int nnz, float *__restrict__ SX) {
+    const int F = fixed_point_exponent(*maxbits, nnz);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < count;
+         i += static_cast<int64_t>(gridDim.x) * kThreads)
+        SX[i] = ldexpf(__ll2float_rn(static_cast<long long>(acc[i])), -F);
 }
 
 // Dense X (n x d, row stride ldx), d % 4 == 0, ldx % 4 == 0, X 16-byte aligned:
@@ -125,8 +152,37 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
     const int need = (nchunks + kWarps - 1) / kWarps;
     const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
     record(ev, true, stream);
-    sketch_csr_atomic_kernel<<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                            SX, status);
+    sketch_csr_kernel<false><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                             SX, nullptr, status);
+    record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+size_t sketch_fixed_scratch_bytes(int64_t B, int d) {
+    return 256 + static_cast<size_t>(B) * d * sizeof(unsigned long long);
+}
+
+cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                    uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, void *scratch,
+                                    int *status, int ctas, const EventPair *ev, cudaStream_t stream) {
+    int *maxbits = static_cast<int *>(scratch);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256);
+    const int64_t cells = static_cast<int64_t>(B) * d;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sketch_fixed_scratch_bytes(B, d), stream);
+    if (e != cudaSuccess) return e;
+    const int sms = num_sms() > 0 ? num_sms() : 148;
+    record(ev, true, stream);
+    if (nnz > 0) absmax_kernel<<<sms * 4, kThreads, 0, stream>>>(vals, nnz, maxbits);
+    if (n > 0) {
+        const int nchunks = (n + 31) / 32;
+        const int need = (nchunks + kWarps - 1) / kWarps;
+        const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
+        sketch_csr_kernel<true><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                                acc, maxbits, status);
+    }
+    const int64_t blocks = (cells + kThreads - 1) / kThreads;
+    fixed_to_float_kernel<<<static_cast<unsigned>(blocks < sms * 8 ? (blocks > 0 ? blocks : 1) : sms * 8), kThreads, 0,
+                            stream>>>(acc, cells, maxbits, nnz, SX);
     record(ev, false, stream);
     return cudaGetLastError();
 }

@@ -5,15 +5,15 @@
 // The B buckets are cut into P ranges ("slices") of SB buckets, SB = floor(32768 / d), so
 // that one slice of SX (SB x d fp32 <= 128 KB) fits in shared memory.
 //
-// Pass 1 (partition): a CTA takes a tile of rows, hashes them once (h, sigma, slice),
-//   and sweeps the tile's nonzeros in batches of up to kBatch.  For each batch it
-//   histograms the records (slice, offset-in-slice = (h mod SB) d + j, sigma x) by
-//   slice in shared memory, reserves one run per slice with a single global atomic,
-//   sorts the batch by slice in shared memory and copies each run out contiguously:
-//   one global atomic per (batch, slice) instead of one reduction per nonzero.
-//   Records beyond a slice's capacity go to an overflow list.
-// Pass 2 (accumulate): one CTA per slice zeroes the slice in shared memory, adds its
-//   records with shared-memory atomics and writes the slice to SX once.
+// Pass 1 (partition): a persistent CTA takes tiles of rows, hashes each row once
+//   (h, sigma, slice), and sorts each batch of the tile's records (slice,
+//   offset-in-slice = (h mod SB) d + j, sigma x) by slice in shared memory -- one
+//   shared-memory atomic per row reserves the row's run -- then appends each slice's
+//   run to its own region of that slice: no global atomics, coalesced copies.
+//   Records beyond a region's capacity go to an overflow list.
+// Pass 2 (accumulate): one CTA per slice zeroes the slice in shared memory, gathers
+//   the slice's records from every pass-1 CTA's region, adds them with shared-memory
+//   atomics and writes the slice to SX once.
 // Pass 3: the overflow list (normally empty) is reduced into SX with global atomics.
 //
 // Record order inside a slice depends on timing, so SX is reproducible only up to
@@ -25,10 +25,10 @@ namespace cg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRows = 1024;        // rows per tile
-constexpr int kBatch = 4096;       // nonzeros per batch
-constexpr int kPerThread = kBatch / kThreads;
-constexpr int kAccThreads = 512;
+constexpr int kRows = 1024;          // rows per tile
+constexpr int kBatch = 4096;         // records per batch (a row never exceeds it: d <= kBatch)
+constexpr int kAccThreads = 1024;
+constexpr int kAccUnroll = 4;        // 16-byte loads in flight per lane in pass 2
 constexpr int kSliceFloats = 32768;  // 128 KB
 
 struct PartParams {
@@ -41,22 +41,29 @@ struct PartParams {
     int64_t row_offset;
 };
 
+// Pass 1.  Per tile of kRows rows: hash every row once.  Then per batch of rows whose
+// nonzeros fit in kBatch: (A) each row reserves its run inside its slice with one
+// shared-memory atomic (its length), (B) the slice counts are scanned into batch
+// offsets and this CTA's region fills, (C) every nonzero is written, coalesced, to its
+// sorted slot: the row's slot plus its position in the row, (D) the runs are copied
+// to this CTA's region of each slice.
 __global__ void __launch_bounds__(kThreads)
 partition_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
                  PartParams pp, int *__restrict__ fills, uint16_t *__restrict__ rkeys, float *__restrict__ rvals,
                  int *__restrict__ ocount, uint32_t *__restrict__ okeys, float *__restrict__ ovals,
                  float *__restrict__ cta_amax, int *__restrict__ status) {
     extern __shared__ __align__(16) uint8_t smem[];
-    int *s_rp = reinterpret_cast<int *>(smem);                    // kRows + 1
-    uint32_t *s_meta = reinterpret_cast<uint32_t *>(s_rp + kRows + 4);  // kRows: base | sign<<15 | slice<<16
-    int *s_cnt = reinterpret_cast<int *>(s_meta + kRows);          // P: records of the batch per slice
-    int *s_off = s_cnt + pp.P;                                     // P: batch offset of each slice
-    int *s_gpos = s_off + pp.P;                                    // P: region fill before the batch
-    int *s_fill = s_gpos + pp.P;                                   // P: region fill so far
-    uint16_t *s_rowid = reinterpret_cast<uint16_t *>(s_fill + pp.P);  // kBatch
-    uint16_t *s_skey = s_rowid + kBatch;                           // kBatch
-    uint16_t *s_spart = s_skey + kBatch;                           // kBatch
-    float *s_sval = reinterpret_cast<float *>(s_spart + kBatch);   // kBatch
+    int *s_rp = reinterpret_cast<int *>(smem);                          // kRows + 1
+    uint32_t *s_meta = reinterpret_cast<uint32_t *>(s_rp + kRows + 4);  // base | sign << 15 | slice << 16
+    int *s_rdst = reinterpret_cast<int *>(s_meta + kRows);              // row's first slot in the batch
+    int *s_cnt = s_rdst + kRows;                                        // P: records of the batch per slice
+    int *s_sbase = s_cnt + pp.P;                                        // P: batch offset of each slice
+    int *s_gpos = s_sbase + pp.P;                                       // P: region fill before the batch
+    int *s_fill = s_gpos + pp.P;                                        // P: region fill so far
+    uint16_t *s_rowid = reinterpret_cast<uint16_t *>(s_fill + pp.P);    // kBatch
+    uint16_t *s_key = s_rowid + kBatch;                                 // kBatch
+    uint16_t *s_part = s_key + kBatch;                                  // kBatch
+    float *s_val = reinterpret_cast<float *>(s_part + kBatch);          // kBatch
     __shared__ int s_warp_sum[kThreads / 32];
     __shared__ float s_warp_max[kThreads / 32];
 
@@ -75,7 +82,7 @@ partition_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_id
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int r0 = tile * kRows;
         const int nr = min(kRows, pp.n - r0);
-        __syncthreads();  // previous tile's readers of s_rp / s_meta are done
+        __syncthreads();  // the previous tile is finished with s_rp / s_meta
         for (int r = t; r <= nr; r += kThreads) s_rp[r] = __ldg(row_ptr + r0 + r);
         for (int r = t; r < nr; r += kThreads) {
             uint32_t h;
@@ -86,46 +93,30 @@ partition_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_id
             s_meta[r] = base | (sg < 0.0f ? 0x8000u : 0u) | (sl << 16);
         }
         __syncthreads();
-        const int kbeg = s_rp[0];
-        const int kend = s_rp[nr];
-        if (kbeg < 0 || kend > pp.nnz || kbeg > kend) {  // malformed row_ptr: skip the tile
+        if (s_rp[0] < 0 || s_rp[nr] > pp.nnz || s_rp[0] > s_rp[nr]) {  // malformed row_ptr: skip the tile
             bad = 1;
             continue;
         }
-        for (int kb = kbeg; kb < kend; kb += kBatch) {
-            const int ke = min(kend, kb + kBatch);
-            const int nb = ke - kb;
-            // nonzero -> row index within the tile
-            for (int r = t; r < nr; r += kThreads) {
-                const int a = max(s_rp[r], kb), e = min(s_rp[r + 1], ke);
-                for (int k = a; k < e; ++k) s_rowid[k - kb] = static_cast<uint16_t>(r);
+        int r = 0;
+        while (r < nr) {
+            // largest re with rp[re] - rp[r] <= kBatch (at least one row)
+            int lo = r + 1, hi = nr;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_rp[mid] - s_rp[r] <= kBatch) lo = mid; else hi = mid - 1;
+            }
+            const int re = lo;
+            const int kb = s_rp[r];
+            const int ke = min(s_rp[re], kb + kBatch);
+            const int nb = max(0, ke - kb);
+            // (A) one run per row inside its slice
+            for (int i = r + t; i < re; i += kThreads) {
+                const int a = max(s_rp[i], kb), e = min(s_rp[i + 1], ke);
+                if (s_rp[i + 1] < s_rp[i]) bad = 1;
+                s_rdst[i] = atomicAdd(&s_cnt[s_meta[i] >> 16], max(0, e - a));
             }
             __syncthreads();
-            uint16_t mkey[kPerThread], mpart[kPerThread], mrank[kPerThread];
-            float mval[kPerThread];
-#pragma unroll
-            for (int j = 0; j < kPerThread; ++j) {
-                const int idx = t + j * kThreads;
-                mpart[j] = 0xFFFFu;
-                if (idx < nb) {
-                    const int k = kb + idx;
-                    const int col = __ldg(col_idx + k);
-                    const float v = __ldg(vals + k);
-                    const uint32_t meta = s_meta[min(static_cast<int>(s_rowid[idx]), nr - 1)];
-                    if (static_cast<unsigned>(col) < static_cast<unsigned>(pp.d)) {
-                        const uint32_t sl = meta >> 16;
-                        mkey[j] = static_cast<uint16_t>((meta & 0x7FFFu) + static_cast<uint32_t>(col));
-                        mval[j] = (meta & 0x8000u) ? -v : v;
-                        amax = fmaxf(amax, fabsf(v));
-                        mpart[j] = static_cast<uint16_t>(sl);
-                        mrank[j] = static_cast<uint16_t>(atomicAdd(&s_cnt[sl], 1));
-                    } else {
-                        bad = 1;
-                    }
-                }
-            }
-            __syncthreads();
-            // exclusive scan of the slice counts; reserve one run per non-empty slice
+            // (B) batch offsets of the slices, region fills of this CTA
             {
                 const int per = (pp.P + kThreads - 1) / kThreads;
                 const int i0 = t * per, i1 = min(pp.P, i0 + per);
@@ -139,51 +130,75 @@ partition_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_id
                 }
                 if (lane == 31) s_warp_sum[warp] = incl;
                 __syncthreads();
-                int wbase = 0;
-                for (int w = 0; w < warp; ++w) wbase += s_warp_sum[w];
-                int run = wbase + incl - sum;
+                int run = incl - sum;
+                for (int w = 0; w < warp; ++w) run += s_warp_sum[w];
                 for (int i = i0; i < i1; ++i) {
                     const int c = s_cnt[i];
-                    s_off[i] = run;
-                    s_gpos[i] = s_fill[i];  // this CTA's own region of slice i: no global atomics
+                    s_sbase[i] = run;
+                    s_gpos[i] = s_fill[i];
                     s_fill[i] += c;
+                    s_cnt[i] = 0;
                     run += c;
                 }
             }
             __syncthreads();
-            // sort the batch by slice in shared memory
-#pragma unroll
-            for (int j = 0; j < kPerThread; ++j) {
-                if (mpart[j] != 0xFFFFu) {
-                    const int pos = s_off[mpart[j]] + mrank[j];
-                    s_skey[pos] = mkey[j];
-                    s_sval[pos] = mval[j];
-                    s_spart[pos] = mpart[j];
-                }
+            // rows: absolute first slot; nonzero -> row map
+            for (int i = r + t; i < re; i += kThreads) {
+                s_rdst[i] += s_sbase[s_meta[i] >> 16];
+                const int a = max(s_rp[i], kb), e = min(s_rp[i + 1], ke);
+                for (int k = a; k < e; ++k) s_rowid[k - kb] = static_cast<uint16_t>(i);
             }
             __syncthreads();
-            // copy out the runs (consecutive records of a slice go to consecutive slots)
-            const int nvalid = s_off[pp.P - 1] + s_cnt[pp.P - 1];
-            for (int i = t; i < nvalid; i += kThreads) {
-                const int sl = s_spart[i];
-                const int64_t dst = static_cast<int64_t>(s_gpos[sl]) + (i - s_off[sl]);
-                if (dst < pp.cap) {
+            // (C) every nonzero to its sorted slot (coalesced loads)
+            for (int idx = t; idx < nb; idx += kThreads) {
+                const int k = kb + idx;
+                const int i = min(max(static_cast<int>(s_rowid[idx]), r), re - 1);
+                const uint32_t meta = s_meta[i];
+                const int col = __ldg(col_idx + k);
+                const float v = __ldg(vals + k);
+                const int pos = s_rdst[i] + (k - max(s_rp[i], kb));
+                if (static_cast<unsigned>(pos) >= static_cast<unsigned>(nb)) {
+                    bad = 1;
+                    continue;
+                }
+                if (static_cast<unsigned>(col) < static_cast<unsigned>(pp.d)) {
+                    s_key[pos] = static_cast<uint16_t>((meta & 0x7FFFu) + static_cast<uint32_t>(col));
+                    s_val[pos] = (meta & 0x8000u) ? -v : v;
+                    amax = fmaxf(amax, fabsf(v));
+                } else {  // a harmless record keeps every reserved slot written
+                    bad = 1;
+                    s_key[pos] = 0;
+                    s_val[pos] = 0.0f;
+                }
+                s_part[pos] = static_cast<uint16_t>(meta >> 16);
+            }
+            __syncthreads();
+            // (D) the runs, contiguous per slice, to this CTA's regions
+            for (int i = t; i < nb; i += kThreads) {
+                const int sl = min(static_cast<int>(s_part[i]), pp.P - 1);
+                const int64_t dst = static_cast<int64_t>(s_gpos[sl]) + (i - s_sbase[sl]);
+                if (dst >= 0 && dst < pp.cap) {
                     const int64_t at = (static_cast<int64_t>(blockIdx.x) * pp.P + sl) * pp.cap + dst;
-                    rkeys[at] = s_skey[i];
-                    rvals[at] = s_sval[i];
+                    rkeys[at] = s_key[i];
+                    rvals[at] = s_val[i];
                 } else {
                     const int o = atomicAdd(ocount, 1);
-                    okeys[o] = static_cast<uint32_t>(sl) * static_cast<uint32_t>(pp.SB) * static_cast<uint32_t>(pp.d) +
-                               s_skey[i];
-                    ovals[o] = s_sval[i];
+                    if (o < pp.nnz) {
+                        okeys[o] = static_cast<uint32_t>(sl) * static_cast<uint32_t>(pp.SB) *
+                                       static_cast<uint32_t>(pp.d) + s_key[i];
+                        ovals[o] = s_val[i];
+                    }
                 }
             }
             __syncthreads();
-            for (int i = t; i < pp.P; i += kThreads) s_cnt[i] = 0;
+            r = re;
         }
     }
     __syncthreads();
-    for (int i = t; i < pp.P; i += kThreads) fills[static_cast<int64_t>(blockIdx.x) * pp.P + i] = s_fill[i];
+    // region fills, clamped to the capacity (the rest went to the overflow list)
+    for (int i = t; i < pp.P; i += kThreads)
+        fills[static_cast<int64_t>(blockIdx.x) * pp.P + i] =
+            static_cast<int>(static_cast<int64_t>(s_fill[i]) < pp.cap ? static_cast<int64_t>(s_fill[i]) : pp.cap);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     if (lane == 0) s_warp_max[warp] = amax;
@@ -196,8 +211,9 @@ partition_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_id
     if (bad) atomicOr(status, kStatusBounds);
 }
 
-// One CTA per slice: gather the slice's records from every pass-1 CTA's region,
-// accumulate them in shared memory, write the slice once.
+// Pass 2: one CTA per slice gathers the slice's records from every pass-1 CTA's
+// region (warp per region, kAccUnroll 16-byte loads in flight per lane), adds them
+// into the slice in shared memory and writes the slice to SX once.
 __global__ void __launch_bounds__(kAccThreads)
 accumulate_kernel(PartParams pp, int nregions, const int *__restrict__ fills, const uint16_t *__restrict__ rkeys,
                   const float *__restrict__ rvals, float *__restrict__ SX, bool vec_out) {
@@ -208,93 +224,51 @@ accumulate_kernel(PartParams pp, int nregions, const int *__restrict__ fills, co
     const int warp = t >> 5;
     const int b0 = sl * pp.SB;
     const int nbk = min(pp.SB, static_cast<int>(pp.B) - b0);
-    const int nf = nbk * pp.d;
-    for (int i = t; i < nf; i += kAccThreads) slice[i] = 0.0f;
+    const unsigned nf = static_cast<unsigned>(nbk * pp.d);
+    for (unsigned i = t; i < nf; i += kAccThreads) slice[i] = 0.0f;
     __syncthreads();
-    // warp w takes regions c = w, w + 16, ...; 4 records per lane-step (regions start
-    // at multiples of 8 records, so uint2 / float4 loads are aligned)
     for (int c = warp; c < nregions; c += kAccThreads / 32) {
         const int64_t reg = static_cast<int64_t>(c) * pp.P + sl;
         const int64_t n = min(static_cast<int64_t>(__ldg(fills + reg)), pp.cap);
         const uint16_t *keys = rkeys + reg * pp.cap;
         const float *vs = rvals + reg * pp.cap;
         const int64_t n4 = n >> 2;
-        for (int64_t q = lane; q < n4; q += 32) {
-            const uint2 k4 = __ldg(reinterpret_cast<const uint2 *>(keys) + q);
-            const float4 v4 = __ldg(reinterpret_cast<const float4 *>(vs) + q);
-            atomicAdd(&slice[k4.x & 0xFFFFu], v4.x);
-            atomicAdd(&slice[k4.x >> 16], v4.y);
-            atomicAdd(&slice[k4.y & 0xFFFFu], v4.z);
-            atomicAdd(&slice[k4.y >> 16], v4.w);
+        for (int64_t q0 = lane; q0 < n4; q0 += 32 * kAccUnroll) {
+            uint2 k4[kAccUnroll];
+            float4 v4[kAccUnroll];
+#pragma unroll
+            for (int u = 0; u < kAccUnroll; ++u) {
+                const int64_t q = q0 + 32 * u;
+                if (q < n4) {
+                    k4[u] = __ldg(reinterpret_cast<const uint2 *>(keys) + q);
+                    v4[u] = __ldg(reinterpret_cast<const float4 *>(vs) + q);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kAccUnroll; ++u) {
+                if (q0 + 32 * u < n4) {
+                    const unsigned k0 = k4[u].x & 0xFFFFu, k1 = k4[u].x >> 16;
+                    const unsigned k2 = k4[u].y & 0xFFFFu, k3 = k4[u].y >> 16;
+                    if (k0 < nf) atomicAdd(&slice[k0], v4[u].x);
+                    if (k1 < nf) atomicAdd(&slice[k1], v4[u].y);
+                    if (k2 < nf) atomicAdd(&slice[k2], v4[u].z);
+                    if (k3 < nf) atomicAdd(&slice[k3], v4[u].w);
+                }
+            }
         }
-        for (int64_t i = (n4 << 2) + lane; i < n; i += 32) atomicAdd(&slice[keys[i]], vs[i]);
+        for (int64_t i = (n4 << 2) + lane; i < n; i += 32) {
+            const unsigned k = keys[i];
+            if (k < nf) atomicAdd(&slice[k], vs[i]);
+        }
     }
     __syncthreads();
     float *dst = SX + static_cast<size_t>(b0) * pp.d;
     if (vec_out) {
-        for (int i = t; i < (nf >> 2); i += kAccThreads)
+        for (unsigned i = t; i < (nf >> 2); i += kAccThreads)
             reinterpret_cast<float4 *>(dst)[i] = reinterpret_cast<const float4 *>(slice)[i];
     } else {
-        for (int i = t; i < nf; i += kAccThreads) dst[i] = slice[i];
+        for (unsigned i = t; i < nf; i += kAccThreads) dst[i] = slice[i];
     }
-}
-
-// Deterministic variant of pass 2.  Every record value v is mapped to the integer
-// q = round(v 2^F) and summed with 64-bit integer atomics, which are associative, so
-// the integer sum is the same whatever order the records arrive in; SX is the single
-// rounding (float)(sum 2^-F).  F = 62 - L - e with 2^e > max|x| (from pass 1) and
-// 2^L > nnz, so no partial sum can leave the int64 range; each term is resolved to
-// 2^(L+e-62) absolute (about 1e-11 of max|x| at nnz ~ 5e7), far finer than fp32
-// accumulation.  Records of this slice that overflowed their region are read from
-// the overflow list here as well.  Inputs must be finite.
-__global__ void __launch_bounds__(kAccThreads)
-accumulate_fixed_kernel(PartParams pp, int nregions, const int *__restrict__ fills,
-                        const uint16_t *__restrict__ rkeys, const float *__restrict__ rvals,
-                        const float *__restrict__ cta_amax, const int *__restrict__ ocount,
-                        const uint32_t *__restrict__ okeys, const float *__restrict__ ovals, float *__restrict__ SX) {
-    extern __shared__ __align__(16) unsigned long long acc[];
-    __shared__ float s_max[kAccThreads / 32];
-    const int sl = blockIdx.x;
-    const int t = threadIdx.x;
-    const int lane = t & 31;
-    const int warp = t >> 5;
-    const int b0 = sl * pp.SB;
-    const int nbk = min(pp.SB, static_cast<int>(pp.B) - b0);
-    const int nf = nbk * pp.d;
-    for (int i = t; i < nf; i += kAccThreads) acc[i] = 0ull;
-    float mx = 0.0f;
-    for (int c = t; c < nregions; c += kAccThreads) mx = fmaxf(mx, __ldg(cta_amax + c));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) s_max[warp] = mx;
-    __syncthreads();
-    mx = 0.0f;
-    for (int w = 0; w < kAccThreads / 32; ++w) mx = fmaxf(mx, s_max[w]);
-    int e = 0;
-    if (mx > 0.0f) frexpf(mx, &e);  // mx < 2^e
-    int L = 1;
-    while ((1LL << L) <= static_cast<int64_t>(pp.nnz)) ++L;  // nnz < 2^L
-    const int F = 62 - L - e;
-    auto fixed = [&](float v) {
-        return static_cast<unsigned long long>(__double2ll_rn(ldexp(static_cast<double>(v), F)));
-    };
-    for (int c = warp; c < nregions; c += kAccThreads / 32) {
-        const int64_t reg = static_cast<int64_t>(c) * pp.P + sl;
-        const int64_t n = min(static_cast<int64_t>(__ldg(fills + reg)), pp.cap);
-        const uint16_t *keys = rkeys + reg * pp.cap;
-        const float *vs = rvals + reg * pp.cap;
-        for (int64_t i = lane; i < n; i += 32) atomicAdd(&acc[keys[i]], fixed(vs[i]));
-    }
-    const int no = *ocount;
-    const uint32_t lo = static_cast<uint32_t>(b0) * static_cast<uint32_t>(pp.d);
-    for (int i = t; i < no; i += kAccThreads) {
-        const uint32_t k = okeys[i];
-        if (k >= lo && k < lo + static_cast<uint32_t>(nf)) atomicAdd(&acc[k - lo], fixed(ovals[i]));
-    }
-    __syncthreads();
-    float *dst = SX + static_cast<size_t>(b0) * pp.d;
-    for (int i = t; i < nf; i += kAccThreads)
-        dst[i] = __double2float_rn(ldexp(static_cast<double>(static_cast<long long>(acc[i])), -F));
 }
 
 __global__ void overflow_kernel(const int *__restrict__ ocount, const uint32_t *__restrict__ okeys,
@@ -308,31 +282,25 @@ __global__ void overflow_kernel(const int *__restrict__ ocount, const uint32_t *
 
 // ---- host side --------------------------------------------------------------------
 
-namespace {
-int slice_floats(bool det) { return det ? kSliceFloats / 2 : kSliceFloats; }  // int64 slices are twice as wide
-}  // namespace
-
 bool partition_supported(const cg_plan &p) {
-    const bool det = p.deterministic != 0;
-    if (p.d > slice_floats(det)) return false;
-    const int64_t SB = slice_floats(det) / p.d;
+    if (p.d > kBatch) return false;
+    const int64_t SB = kSliceFloats / p.d;
     const int64_t P = (p.B + SB - 1) / SB;
     return P <= 4096 && p.B * static_cast<int64_t>(p.d) < (1LL << 32) && p.n < (1LL << 31) - 1;
 }
 
 size_t partition_smem(int P) {
-    return static_cast<size_t>(kRows + 4) * 4 + kRows * 4 + 4 * static_cast<size_t>(P) * 4 +
+    return static_cast<size_t>(kRows + 4) * 4 + 2 * kRows * 4 + 4 * static_cast<size_t>(P) * 4 +
            static_cast<size_t>(kBatch) * (2 + 2 + 2 + 4);
 }
 
 PartLayout partition_layout(const cg_plan &p, int64_t nnz) {
     PartLayout L{};
-    L.det = p.deterministic != 0;
-    L.SB = slice_floats(L.det) / p.d;
+    L.SB = kSliceFloats / p.d;
     L.P = static_cast<int>((p.B + L.SB - 1) / L.SB);
     const int sms = num_sms() > 0 ? num_sms() : 148;
     int per_sm = static_cast<int>((200 * 1024) / (partition_smem(L.P) + 2048));
-    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
     const int64_t ntiles = (p.n + kRows - 1) / kRows;
     L.G = static_cast<int>(ntiles < sms * per_sm ? (ntiles > 0 ? ntiles : 1) : sms * per_sm);
     // one region per (pass-1 CTA, slice); records beyond a region go to the overflow list
@@ -375,29 +343,18 @@ cudaError_t launch_sketch_csr_partitioned(const int *row_ptr, const int *col_idx
     if ((e = cudaFuncSetAttribute(partition_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(smem1))) != cudaSuccess)
         return e;
-    const size_t smem2 = static_cast<size_t>(L.SB) * d * (L.det ? sizeof(unsigned long long) : sizeof(float));
-    if (L.det) {
-        if ((e = cudaFuncSetAttribute(accumulate_fixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem2))) != cudaSuccess)
-            return e;
-    } else if ((e = cudaFuncSetAttribute(accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem2))) != cudaSuccess) {
+    const size_t smem2 = static_cast<size_t>(L.SB) * d * sizeof(float);
+    if ((e = cudaFuncSetAttribute(accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem2))) != cudaSuccess)
         return e;
-    }
     const bool vec_out = d % 4 == 0 && (reinterpret_cast<uintptr_t>(SX) & 15) == 0;
     record(ev, true, stream);
     // every pass-1 CTA runs (even without tiles) so that all region fills are written
     partition_kernel<<<L.G, kThreads, smem1, stream>>>(row_ptr, col_idx, vals, pp, fills, rkeys, rvals, ocount, okeys,
                                                        ovals, amax, status);
-    if (L.det) {
-        accumulate_fixed_kernel<<<L.P, kAccThreads, smem2, stream>>>(pp, L.G, fills, rkeys, rvals, amax, ocount,
-                                                                     okeys, ovals, SX);
-        record(ev, false, stream);
-    } else {
-        accumulate_kernel<<<L.P, kAccThreads, smem2, stream>>>(pp, L.G, fills, rkeys, rvals, SX, vec_out);
-        record(ev, false, stream);
-        overflow_kernel<<<sms, 256, 0, stream>>>(ocount, okeys, ovals, SX);
-    }
+    accumulate_kernel<<<L.P, kAccThreads, smem2, stream>>>(pp, L.G, fills, rkeys, rvals, SX, vec_out);
+    record(ev, false, stream);
+    overflow_kernel<<<sms, 256, 0, stream>>>(ocount, okeys, ovals, SX);
     return cudaGetLastError();
 }
 
