@@ -191,6 +191,29 @@ CG_API cg_status cg_sketch_dense(cg_plan *plan, const float *X, int64_t ldx, flo
 CG_API cg_status cg_contract(cg_plan *plan, const float *SX, float *Y,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* ---- NMF anchors (Algorithm 1) ---------------------------------------------------- */
+
+/* Algorithm 1 step 3: imax[r] / imin[r] = column index of the largest / smallest
+ * entry of row r of Z (device, m x d fp32 row-major), lowest index on ties.  imax,
+ * imin: device int32[m]. */
+CG_API cg_status cg_row_argmax_argmin(const float *Z, int32_t m, int32_t d, int32_t *imax, int32_t *imin,
+                                      void *stream);
+
+/* Algorithm 1 steps 1-3 for CSR X: Z = T.X as cg_apply_csr (Z device m x d, workspace
+ * of CG_OP_APPLY_CSR), then the row argmax / argmin of Z. */
+CG_API cg_status cg_nmf_anchors_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                                    int64_t nnz, float *Z, int32_t *imax, int32_t *imin, void *ws, size_t ws_bytes,
+                                    void *stream);
+
+/* ---- distribution checker ----------------------------------------------------------- */
+
+/* FP64 reductions over sample rows Y (device, rows x d fp32 row-major), accumulated
+ * into caller buffers (device, zeroed by the caller before the first call):
+ *   gram[d x d] += Y^T Y   and   sumsq[0] += ||Y||_F^2   (either may be NULL).
+ * Used to check the distributions of Section 7 and Theorem 1 (rows of G.S.X given S
+ * are N(0, X^T S^T S X); rows of G~.X are N(0, X^T X)) on the device's own samples. */
+CG_API cg_status cg_moments_f64(const float *Y, int64_t rows, int32_t d, double *gram, double *sumsq, void *stream);
+
 /* ---- many instances in one launch ------------------------------------------------ */
 
 /* One CountGauss instance of a batch: its own plan parameters (as cg_plan_create),

@@ -162,6 +162,23 @@ class CountGauss:
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
         return Y
 
+    def nmf_anchors(self, row_ptr, col_idx, vals):
+        """Algorithm 1 steps 1-3: Z = T.X and, per row of Z, the column of its max and
+        of its min (lowest index on ties).  Returns (Z, imax, imin)."""
+        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        col_idx = _need(col_idx, torch.int32, "col_idx")
+        vals = _need(vals, torch.float32, "vals")
+        dev = row_ptr.device
+        nnz = col_idx.numel()
+        Z = torch.empty(self.m, self.d, dtype=torch.float32, device=dev)
+        imax = torch.empty(self.m, dtype=torch.int32, device=dev)
+        imin = torch.empty(self.m, dtype=torch.int32, device=dev)
+        ws = self.workspace(_lib.OP_APPLY_CSR, nnz, dev)
+        _lib.check("cg_nmf_anchors_csr", self._lib.cg_nmf_anchors_csr(
+            self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Z), _ptr(imax), _ptr(imin), _ptr(ws),
+            ws.numel(), _stream(dev)))
+        return Z, imax, imin
+
     # -- stages -----------------------------------------------------------------
     def sketch_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
         row_ptr = _need(row_ptr, torch.int32, "row_ptr")
@@ -266,6 +283,30 @@ class CountGaussBatch:
         _lib.check("cg_batch_autotune", self._lib.cg_batch_autotune(self._h, _ptr(ws), ws.numel(),
                                                                     _stream(self.device), reps, ctypes.byref(best)))
         return float(best.value)
+
+
+# -- distribution checker -------------------------------------------------------------
+def moments_f64(Y: torch.Tensor, gram: torch.Tensor | None = None, sumsq: torch.Tensor | None = None):
+    """gram += Y^T Y and sumsq += ||Y||_F^2 in FP64 on the device (cg_moments_f64).
+    Y: CUDA float32 (rows, d).  New zeroed accumulators are made when not given."""
+    Y = _need(Y, torch.float32, "Y")
+    d = Y.shape[1]
+    if gram is None:
+        gram = torch.zeros(d, d, dtype=torch.float64, device=Y.device)
+    if sumsq is None:
+        sumsq = torch.zeros(1, dtype=torch.float64, device=Y.device)
+    _lib.call("cg_moments_f64", _ptr(Y), Y.shape[0], d, _ptr(gram), _ptr(sumsq), _stream(Y.device))
+    return gram, sumsq
+
+
+def row_argmax_argmin(Z: torch.Tensor):
+    """Algorithm 1 step 3 on a device matrix Z (m x d): (imax, imin), int32."""
+    Z = _need(Z, torch.float32, "Z")
+    m, d = Z.shape
+    imax = torch.empty(m, dtype=torch.int32, device=Z.device)
+    imin = torch.empty(m, dtype=torch.int32, device=Z.device)
+    _lib.call("cg_row_argmax_argmin", _ptr(Z), m, d, _ptr(imax), _ptr(imin), _stream(Z.device))
+    return imax, imin
 
 
 # -- generator dumps (bit-exact checks against the oracle) -----------------------

@@ -36,35 +36,38 @@ contract_ffma_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key 
                           part + static_cast<size_t>(blockIdx.x) * m * d, raw);
 }
 
-// Y[o] = sum over s of part[s][o], s in increasing order within each of 8 lanes,
-// then the 8 lane sums in increasing lane order.
-__global__ void __launch_bounds__(256)
+// Y[o] = sum over s of part[s][o]: 32 outputs per CTA (lanes, coalesced), 32 warps
+// each summing every 32nd partial in increasing s, then the 32 warp sums in
+// increasing warp order -- a fixed order, so Y is reproducible for a given grid.
+constexpr int kRedWarps = 32;
+
+__global__ void __launch_bounds__(kRedWarps * 32)
 reduce_splits_kernel(const float *__restrict__ part, int nsplit, int64_t total, float *__restrict__ Y) {
-    __shared__ float red[8][33];
+    __shared__ float red[kRedWarps][33];
     const int lane = threadIdx.x & 31;
     const int sl = threadIdx.x >> 5;
     const int64_t o = static_cast<int64_t>(blockIdx.x) * 32 + lane;
     float acc = 0.0f;
     if (o < total) {
         int s = sl;
-        for (; s + 24 < nsplit; s += 32) {
+        for (; s + 3 * kRedWarps < nsplit; s += 4 * kRedWarps) {
             const float a0 = __ldg(part + static_cast<size_t>(s) * total + o);
-            const float a1 = __ldg(part + static_cast<size_t>(s + 8) * total + o);
-            const float a2 = __ldg(part + static_cast<size_t>(s + 16) * total + o);
-            const float a3 = __ldg(part + static_cast<size_t>(s + 24) * total + o);
+            const float a1 = __ldg(part + static_cast<size_t>(s + kRedWarps) * total + o);
+            const float a2 = __ldg(part + static_cast<size_t>(s + 2 * kRedWarps) * total + o);
+            const float a3 = __ldg(part + static_cast<size_t>(s + 3 * kRedWarps) * total + o);
             acc += a0;
             acc += a1;
             acc += a2;
             acc += a3;
         }
-        for (; s < nsplit; s += 8) acc += __ldg(part + static_cast<size_t>(s) * total + o);
+        for (; s < nsplit; s += kRedWarps) acc += __ldg(part + static_cast<size_t>(s) * total + o);
     }
     red[sl][lane] = acc;
     __syncthreads();
     if (sl == 0 && o < total) {
         float r = red[0][lane];
 #pragma unroll
-        for (int q = 1; q < 8; ++q) r += red[q][lane];
+        for (int q = 1; q < kRedWarps; ++q) r += red[q][lane];
         Y[o] = r;
     }
 }
@@ -91,7 +94,7 @@ size_t contract_partials_bytes(const cg_plan &p) {
 cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream) {
     if (total == 0) return cudaSuccess;
     const int64_t grid = (total + 31) / 32;
-    reduce_splits_kernel<<<static_cast<unsigned>(grid), 256, 0, stream>>>(partials, nsplit, total, Y);
+    reduce_splits_kernel<<<static_cast<unsigned>(grid), kRedWarps * 32, 0, stream>>>(partials, nsplit, total, Y);
     return cudaGetLastError();
 }
 

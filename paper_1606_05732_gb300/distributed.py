@@ -1,0 +1,95 @@
+"""Sharded CountGauss over torch.distributed (the distributed remark of Section 4).
+
+Every process that shares the seed holds the same T: h, sigma and the columns of G~
+are functions of (seed, global row index), G of the seed alone.  Two layouts follow:
+
+* Row shards (features): rank p holds rows [start_p, stop_p) of X and computes
+  T_p X_p with row offset start_p; T X is the sum over ranks -- one all-reduce of the
+  m x d output (sum_outputs).
+* Column shards (data points, as in the paper's NMF setting where each server holds
+  some of the points): every rank holds all rows and some columns, computes its own
+  columns of Z = T X, finds per row the max / min over its columns (with global column
+  indices), and a coordinator keeps the largest / smallest, the lowest global index on
+  ties (merge_anchor_records).
+
+The functions here are host logic (sharding, offsets, the collective, the merge); the
+per-rank compute is the library's (or, in the CPU tests, the oracle's).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.distributed as dist
+
+
+def shard_range(total: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous near-equal shard [start, stop) of `total` items for `rank`."""
+    base, extra = divmod(total, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
+def shard_csr_rows(row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray, start: int, stop: int):
+    """Rows [start, stop) of a CSR matrix with row_ptr rebased to 0."""
+    a, b = int(row_ptr[start]), int(row_ptr[stop])
+    return row_ptr[start:stop + 1] - a, col_idx[a:b], vals[a:b]
+
+
+def shard_csr_cols(row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray, start: int, stop: int):
+    """Columns [start, stop) of a CSR matrix (all rows), column indices rebased to 0."""
+    keep = (col_idx >= start) & (col_idx < stop)
+    rows = np.repeat(np.arange(row_ptr.size - 1), np.diff(row_ptr))[keep]
+    rp = np.zeros(row_ptr.size, row_ptr.dtype)
+    np.cumsum(np.bincount(rows, minlength=row_ptr.size - 1), out=rp[1:])
+    return rp, (col_idx[keep] - start).astype(col_idx.dtype), vals[keep]
+
+
+def sum_outputs(Y: torch.Tensor, group=None) -> torch.Tensor:
+    """In-place sum of the per-rank m x d outputs (row shards)."""
+    dist.all_reduce(Y, op=dist.ReduceOp.SUM, group=group)
+    return Y
+
+
+def local_anchor_records(Z: np.ndarray, col_start: int) -> np.ndarray:
+    """Per row of a rank's columns of Z: (max value, global column of the max,
+    min value, global column of the min), lowest column on ties.  Shape (m, 4), float64."""
+    m, d = Z.shape
+    rec = np.full((m, 4), np.nan)
+    if d == 0:
+        return rec
+    jmax = np.argmax(Z, axis=1)
+    jmin = np.argmin(Z, axis=1)
+    rec[:, 0] = Z[np.arange(m), jmax]
+    rec[:, 1] = jmax + col_start
+    rec[:, 2] = Z[np.arange(m), jmin]
+    rec[:, 3] = jmin + col_start
+    return rec
+
+
+def merge_anchor_records(records: list[np.ndarray]) -> tuple[np.ndarray, np.ndarray]:
+    """Coordinator merge of the ranks' records: global (imax, imin) per row."""
+    m = records[0].shape[0]
+    imax = np.zeros(m, np.int64)
+    imin = np.zeros(m, np.int64)
+    for r in range(m):
+        best = None
+        worst = None
+        for rec in records:
+            v, j, w, k = rec[r]
+            if np.isnan(v):
+                continue
+            if best is None or v > best[0] or (v == best[0] and j < best[1]):
+                best = (v, j)
+            if worst is None or w < worst[0] or (w == worst[0] and k < worst[1]):
+                worst = (w, k)
+        imax[r] = int(best[1])
+        imin[r] = int(worst[1])
+    return imax, imin
+
+
+def gather_anchor_records(rec: np.ndarray, group=None) -> list[np.ndarray]:
+    """All ranks' records (every rank receives all, so any rank can act as coordinator)."""
+    t = torch.from_numpy(np.ascontiguousarray(rec, np.float64))
+    out = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(out, t, group=group)
+    return [o.numpy() for o in out]
