@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scatter", choices=["auto", "atomic", "partition"], default="auto")
+    ap.add_argument("--scatter-passes", type=int, default=0, help="bucket-range passes of the scatter (0: automatic)")
+    ap.add_argument("--scatter-rows", type=int, default=0, choices=[0, 32, 64, 128],
+                    help="CSR rows per warp chunk of the scatter (0: automatic)")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
     return ap.parse_args()
 
@@ -322,7 +325,8 @@ def run_ours(args):
     ci_h = torch.from_numpy(X.col_idx).pin_memory()
     v_h = torch.from_numpy(X.vals).pin_memory()
     rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
-    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter)
+    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter,
+                                 scatter_passes=args.scatter_passes, scatter_rows=args.scatter_rows)
     partitioned = args.scatter == "partition"  # auto: the atomic scatter
     scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_atomic_kernel")
     scatter_src = ("cg_sketch_part.cu", "cg_rng.cuh") if partitioned else ("cg_sketch.cu", "cg_rng.cuh")

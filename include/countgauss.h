@@ -86,16 +86,23 @@ typedef enum cg_precision {
 
 typedef enum cg_option {
     CG_OPT_PRECISION = 1,     /* cg_precision of the Gaussian contraction (default FP32) */
-    CG_OPT_DETERMINISTIC = 2, /* 0: atomic scatter (default); 1: sort-by-bucket scatter,
-                                 bit-reproducible run to run */
+    CG_OPT_DETERMINISTIC = 2, /* 0: fp32 atomic scatter (default); 1: exact int64 fixed-point
+                                 sums of the scatter, rounded once to fp32: independent of
+                                 the order of the reductions, so bit-reproducible run to run */
     CG_OPT_ROW_OFFSET = 3,    /* global index of local row 0 (default 0) */
     CG_OPT_KSPLIT = 4,        /* CTAs along B in the contraction; 0 = automatic */
     CG_OPT_SKETCH_CTAS = 5,   /* CTAs of the scatter kernel; 0 = automatic */
     CG_OPT_TIMING = 6,        /* 1: record CUDA events around each main kernel launch
                                  (read with cg_plan_timing); 0 (default): off */
-    CG_OPT_SCATTER = 7        /* CSR scatter algorithm (atomic mode): 0 = automatic (default),
+    CG_OPT_SCATTER = 7,       /* CSR scatter algorithm (atomic mode): 0 = automatic (default),
                                  1 = one L2 reduction per nonzero, 2 = partition the nonzeros by
                                  bucket range and accumulate each range in shared memory */
+    CG_OPT_SCATTER_PASSES = 8, /* bucket-range passes of the atomic CSR scatter (each pass streams
+                                 the CSR and reduces the rows of one range of buckets, keeping
+                                 that range of SX in L2); 0 = automatic (one pass), 1..16 forced */
+    CG_OPT_SCATTER_ROWS = 9   /* CSR rows per warp chunk of the scatter: 0 = automatic (the
+                                 smallest of 32, 64, 128 whose chunk holds about 96 nonzeros on
+                                 average), or 32, 64, 128 forced */
 } cg_option;
 
 typedef enum cg_kernel {

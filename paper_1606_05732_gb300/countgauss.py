@@ -48,7 +48,7 @@ class CountGauss:
 
     def __init__(self, n: int, d: int, m: int, B: int, seed: int, *, precision: str = "fp32",
                  deterministic: bool = False, row_offset: int = 0, ksplit: int = 0, sketch_ctas: int = 0,
-                 scatter: str = "auto"):
+                 scatter: str = "auto", scatter_passes: int = 0, scatter_rows: int = 0):
         lib = _lib.load()
         h = _P()
         _lib.check("cg_plan_create", lib.cg_plan_create(n, d, m, B, seed, ctypes.byref(h)))
@@ -62,6 +62,8 @@ class CountGauss:
         self.set_option(_lib.OPT_KSPLIT, int(ksplit))
         self.set_option(_lib.OPT_SKETCH_CTAS, int(sketch_ctas))
         self.set_option(_lib.OPT_SCATTER, _lib.SCATTER[scatter])
+        self.set_option(_lib.OPT_SCATTER_PASSES, int(scatter_passes))
+        self.set_option(_lib.OPT_SCATTER_ROWS, int(scatter_rows))
         self.precision = precision
         self.deterministic = bool(deterministic)
         self.row_offset = int(row_offset)

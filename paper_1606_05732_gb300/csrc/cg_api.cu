@@ -254,7 +254,8 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
         return from_cuda(launch_sketch_csr_fixed(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                                  static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
                                                  p->row_offset, SX, region(ws, L.c_off), status_word(ws),
-                                                 static_cast<int>(p->sketch_ctas), timing_pair(p, CG_KERNEL_SKETCH), st));
+                                                 static_cast<int>(p->sketch_ctas), p->scatter_rows,
+                                                 timing_pair(p, CG_KERNEL_SKETCH), st));
     if (use_partition(*p))
         return from_cuda(launch_sketch_csr_partitioned(
             row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), static_cast<int>(nnz),
@@ -263,7 +264,7 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
     return from_cuda(launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                               static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
                                               p->row_offset, SX, status_word(ws), static_cast<int>(p->sketch_ctas),
-                                              timing_pair(p, CG_KERNEL_SKETCH), st));
+                                              p->scatter_passes, p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st));
 }
 
 }  // namespace
@@ -305,6 +306,8 @@ cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t se
     p->timing = 0;
     p->timing_state = nullptr;
     p->scatter = 0;
+    p->scatter_passes = 0;
+    p->scatter_rows = 0;
     *out = p;
     return CG_OK;
 }
@@ -372,6 +375,14 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             if (value < 0 || value > 2) return CG_ERR_INVALID_ARG;
             p->scatter = static_cast<int32_t>(value);
             return CG_OK;
+        case CG_OPT_SCATTER_PASSES:
+            if (value < 0 || value > 16) return CG_ERR_INVALID_ARG;
+            p->scatter_passes = static_cast<int32_t>(value);
+            return CG_OK;
+        case CG_OPT_SCATTER_ROWS:
+            if (value != 0 && value != 32 && value != 64 && value != 128) return CG_ERR_INVALID_ARG;
+            p->scatter_rows = static_cast<int32_t>(value);
+            return CG_OK;
         default:
             return CG_ERR_INVALID_ARG;
     }
@@ -387,6 +398,8 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
         case CG_OPT_SKETCH_CTAS: *value = p->sketch_ctas; return CG_OK;
         case CG_OPT_TIMING: *value = p->timing; return CG_OK;
         case CG_OPT_SCATTER: *value = p->scatter; return CG_OK;
+        case CG_OPT_SCATTER_PASSES: *value = p->scatter_passes; return CG_OK;
+        case CG_OPT_SCATTER_ROWS: *value = p->scatter_rows; return CG_OK;
         default: return CG_ERR_INVALID_ARG;
     }
 }

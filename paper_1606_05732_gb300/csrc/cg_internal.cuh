@@ -22,6 +22,8 @@ struct cg_plan {
     int32_t timing;         // CG_OPT_TIMING
     void *timing_state;     // cg::TimingState*, created on first timed launch
     int32_t scatter;        // CG_OPT_SCATTER
+    int32_t scatter_passes; // CG_OPT_SCATTER_PASSES (0 = auto)
+    int32_t scatter_rows;   // CG_OPT_SCATTER_ROWS (0 = auto)
 };
 
 namespace cg {
@@ -54,7 +56,7 @@ int num_sms();
 // ---- scatter (cg_sketch.cu) -------------------------------------------------
 cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                     int ctas, const EventPair *ev, cudaStream_t stream);
+                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream);
 cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d, uint32_t B, Key key,
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
                                        cudaStream_t stream);
@@ -63,7 +65,7 @@ int sketch_default_ctas();
 size_t sketch_fixed_scratch_bytes(int64_t B, int d);
 cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, void *scratch,
-                                    int *status, int ctas, const EventPair *ev, cudaStream_t stream);
+                                    int *status, int ctas, int rows, const EventPair *ev, cudaStream_t stream);
 
 // ---- partitioned scatter (cg_sketch_part.cu) --------------------------------------
 struct PartLayout {

@@ -79,7 +79,7 @@ extern "C" cg_status cg_apply_csr_noalloc(cg_plan *p, const int32_t *row_ptr, co
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return CG_ERR_CUDA;
     if (launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
                                  static_cast<int>(nnz), make_key(p->seed), p->row_offset, SX, status,
-                                 static_cast<int>(p->sketch_ctas), nullptr, st) != cudaSuccess)
+                                 static_cast<int>(p->sketch_ctas), p->scatter_passes, p->scatter_rows, nullptr, st) != cudaSuccess)
         return CG_ERR_CUDA;
     if (launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), nsplit, partials, Y, nullptr, st) !=
         cudaSuccess)

@@ -56,34 +56,46 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, int F) {
     return static_cast<unsigned long long>((u >> 31) ? -q : q);
 }
 
-// Rows [first, min(first + 32, n)) of a CSR matrix: lane l hashes row first + l and
-// loads its row_ptr entry into the warp's shared arrays s_rp[33], s_h[32], s_sg[32];
-// the rows' nonzeros [beg, end) are swept 32 x kScatterUnroll at a time with coalesced
-// evict-first loads, each nonzero finds its row by a 5-step binary search over s_rp and
-// becomes one reduction into SX: fp32, or with FIXED the 64-bit integer to_fixed(x, F)
-// into an integer SX (order-independent sums).  Out-of-range column indices and
-// malformed row offsets are skipped and reported through `bad`.
-template <bool FIXED>
-__device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
-                                                const float *__restrict__ vals, int first, int n, int d, uint32_t B,
-                                                int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
-                                                int *s_rp, uint32_t *s_h, float *s_sg, int &bad) {
+// Rows [first, min(first + ROWS, n)) of a CSR matrix (ROWS = 32, 64 or 128): lane l
+// loads the row_ptr entries of rows first + l + 32 r and hashes those rows into the
+// warp's shared arrays s_rp[ROWS + 1], s_h[ROWS], s_sg[ROWS]; the rows' nonzeros
+// [beg, end) are swept 32 x kScatterUnroll at a time with coalesced evict-first loads,
+// each nonzero finds its row by a log2(ROWS)-step binary search over s_rp and becomes
+// one reduction into SX: fp32, or with FIXED the 64-bit integer to_fixed(x, F) into an
+// integer SX (order-independent sums).  Taller chunks put more nonzeros behind each
+// pair of dependent memory round trips (row_ptr, then the nonzeros), which is what
+// very sparse rows need.  Out-of-range column indices and malformed row offsets are
+// skipped and reported through `bad`.  Only rows whose bucket lies in [blo, bhi) are
+// reduced (bucket-range passes); blo = 0, bhi = B reduces every row.
+template <bool FIXED, int ROWS>
+__device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                                              const float *__restrict__ vals, int first, int n, int d, uint32_t B,
+                                              int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
+                                              int *s_rp, uint32_t *s_h, float *s_sg, int &bad, uint32_t blo = 0u,
+                                              uint32_t bhi = 0xFFFFFFFFu) {
+    static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128, "chunk height");
+    constexpr int R = ROWS / 32;
     const int lane = threadIdx.x & 31;
     const uint64_t pol = l2_evict_first_policy();
-    const int i = first + lane;
-    const int last = min(first + 32, n);
+    const int last = min(first + ROWS, n);
     const int end = __ldg(row_ptr + last);
-    int rp = end;
-    uint32_t h = 0;
-    float sg = 0.0f;
-    if (i < n) {
-        rp = ld_stream_i32(row_ptr + i, pol);
-        hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+    int rp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {  // all row_ptr loads in flight before the hashing
+        const int i = first + r * 32 + lane;
+        rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
     }
-    s_rp[lane] = rp;
-    s_h[lane] = h;
-    s_sg[lane] = sg;
-    if (lane == 0) s_rp[32] = end;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = first + r * 32 + lane;
+        uint32_t h = 0;
+        float sg = 0.0f;
+        if (i < n) hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+        s_rp[r * 32 + lane] = rp[r];
+        s_h[r * 32 + lane] = h;
+        s_sg[r * 32 + lane] = sg;
+    }
+    if (lane == 0) s_rp[ROWS] = end;
     __syncwarp();
     const int beg = s_rp[0];
     if (beg < 0 || end > nnz || beg > end) {  // malformed row_ptr: skip the chunk
@@ -99,22 +111,25 @@ __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr,
             const int k = k0 + u * 32 + lane;
             col[u] = -1;
             v[u] = 0.0f;
-            if (k < end) {
+            if (k0 + u * 32 < end && k < end) {  // first test warp-uniform: empty slots cost nothing
                 col[u] = ld_stream_i32(col_idx + k, pol);
                 v[u] = ld_stream_f32(vals + k, pol);
             }
         }
 #pragma unroll
         for (int u = 0; u < kScatterUnroll; ++u) {
+            if (k0 + u * 32 >= end) break;  // warp-uniform
             const int k = k0 + u * 32 + lane;
             if (k < end) {
                 int lo = 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
+                for (int step = ROWS / 2; step > 0; step >>= 1)
                     if (s_rp[lo + step] <= k) lo += step;
                 const int j = col[u];
+                const uint32_t hb = s_h[lo];
+                if (hb < blo || hb >= bhi) continue;  // another pass reduces this row
                 if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
-                    const size_t at = static_cast<size_t>(s_h[lo]) * d + j;
+                    const size_t at = static_cast<size_t>(hb) * d + j;
                     if (FIXED)
                         atomicAdd(static_cast<unsigned long long *>(SX) + at, to_fixed(s_sg[lo] * v[u], F));
                     else
@@ -126,6 +141,16 @@ __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr,
         }
     }
     __syncwarp();
+}
+
+// The 32-row chunk (one row per lane).
+template <bool FIXED>
+__device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                                                const float *__restrict__ vals, int first, int n, int d, uint32_t B,
+                                                int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
+                                                int *s_rp, uint32_t *s_h, float *s_sg, int &bad) {
+    scatter_chunk<FIXED, 32>(row_ptr, col_idx, vals, first, n, d, B, nnz, key, row_offset, SX, F, s_rp, s_h, s_sg,
+                             bad);
 }
 
 }  // namespace cg

@@ -18,25 +18,50 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kUnroll = 4;  // nonzeros in flight per lane
 
-// One warp owns a chunk of 32 consecutive rows at a time (scatter_chunk32): lane l
-// hashes row l of the chunk, the chunk's nonzeros are swept with coalesced loads and
-// each becomes one reduction into SX (fp32; with FIXED, int64 fixed point).
-template <bool FIXED>
+// One warp owns a chunk of ROWS consecutive rows at a time (scatter_chunk): the
+// chunk's rows are hashed by its lanes, its nonzeros are swept with coalesced loads
+// and each becomes one reduction into SX (fp32; with FIXED, int64 fixed point).
+template <bool FIXED, int ROWS>
 __global__ void __launch_bounds__(kThreads)
 sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
                   int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *__restrict__ SX,
-                  const int *__restrict__ maxbits, int *__restrict__ status) {
-    __shared__ int s_rp[kWarps][33];
-    __shared__ uint32_t s_h[kWarps][32];
-    __shared__ float s_sg[kWarps][32];
+                  const int *__restrict__ maxbits, int *__restrict__ status, uint32_t blo, uint32_t bhi) {
+    __shared__ int s_rp[kWarps][ROWS + 1];
+    __shared__ uint32_t s_h[kWarps][ROWS];
+    __shared__ float s_sg[kWarps][ROWS];
     const int w = threadIdx.x >> 5;
-    const int nchunks = (n + 31) >> 5;
+    const int nchunks = (n + ROWS - 1) / ROWS;
     const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
     int bad = 0;
     for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps)
-        scatter_chunk32<FIXED>(row_ptr, col_idx, vals, c << 5, n, d, B, nnz, key, row_offset, SX, F, s_rp[w], s_h[w],
-                               s_sg[w], bad);
+        scatter_chunk<FIXED, ROWS>(row_ptr, col_idx, vals, c * ROWS, n, d, B, nnz, key, row_offset, SX, F, s_rp[w],
+                                   s_h[w], s_sg[w], bad, blo, bhi);
     if (bad) atomicOr(status, kStatusBounds);
+}
+
+// Rows per warp chunk: `forced` (32, 64 or 128) or, for 0, the smallest height whose
+// chunk holds about 96 nonzeros on average (a few 32-wide sweeps per round trip).
+int chunk_rows(int n, int nnz, int forced) {
+    if (forced == 32 || forced == 64 || forced == 128) return forced;
+    const double per_row = n > 0 ? static_cast<double>(nnz) / n : 0.0;
+    if (per_row * 32 >= 96.0) return 32;
+    if (per_row * 64 >= 96.0) return 64;
+    return 128;
+}
+
+template <bool FIXED>
+void launch_csr_rows(int rows, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
+                     const float *vals, int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *SX,
+                     const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
+    if (rows == 128)
+        sketch_csr_kernel<FIXED, 128><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                     row_offset, SX, maxbits, status, blo, bhi);
+    else if (rows == 64)
+        sketch_csr_kernel<FIXED, 64><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                    row_offset, SX, maxbits, status, blo, bhi);
+    else
+        sketch_csr_kernel<FIXED, 32><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                    row_offset, SX, maxbits, status, blo, bhi);
 }
 
 // max |x| over the stored values, as the bit pattern of a non-negative float (whose
@@ -145,15 +170,27 @@ int sketch_default_ctas() {
 
 cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                     int ctas, const EventPair *ev, cudaStream_t stream) {
+                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
     if (e != cudaSuccess || n == 0) return e;
-    const int nchunks = (n + 31) / 32;
+    rows = chunk_rows(n, nnz, rows);
+    const int nchunks = (n + rows - 1) / rows;
     const int need = (nchunks + kWarps - 1) / kWarps;
     const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
     record(ev, true, stream);
-    sketch_csr_kernel<false><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                             SX, nullptr, status);
+    // Optionally the buckets are reduced in ranges, one pass over the CSR per range, so
+    // that each range's reductions stay in L2.  Automatic is one pass: on GB300 extra
+    // passes cost more (every pass re-streams the CSR and re-hashes every row) than the
+    // L2 misses they save, even with SX at 134 MB.
+    if (passes <= 0) passes = 1;
+    if (static_cast<uint32_t>(passes) > B) passes = B > 0 ? static_cast<int>(B) : 1;
+    const uint32_t per = static_cast<uint32_t>((static_cast<uint64_t>(B) + passes - 1) / passes);
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t blo = per * static_cast<uint32_t>(p);
+        const uint32_t bhi = p == passes - 1 ? B : blo + per;
+        launch_csr_rows<false>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, nullptr,
+                               status, blo, bhi);
+    }
     record(ev, false, stream);
     return cudaGetLastError();
 }
@@ -164,7 +201,7 @@ size_t sketch_fixed_scratch_bytes(int64_t B, int d) {
 
 cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, void *scratch,
-                                    int *status, int ctas, const EventPair *ev, cudaStream_t stream) {
+                                    int *status, int ctas, int rows, const EventPair *ev, cudaStream_t stream) {
     int *maxbits = static_cast<int *>(scratch);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256);
     const int64_t cells = static_cast<int64_t>(B) * d;
@@ -174,11 +211,12 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
     record(ev, true, stream);
     if (nnz > 0) absmax_kernel<<<sms * 4, kThreads, 0, stream>>>(vals, nnz, maxbits);
     if (n > 0) {
-        const int nchunks = (n + 31) / 32;
+        rows = chunk_rows(n, nnz, rows);
+        const int nchunks = (n + rows - 1) / rows;
         const int need = (nchunks + kWarps - 1) / kWarps;
         const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
-        sketch_csr_kernel<true><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                                acc, maxbits, status);
+        launch_csr_rows<true>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, acc, maxbits,
+                              status, 0u, B);
     }
     const int64_t blocks = (cells + kThreads - 1) / kThreads;
     fixed_to_float_kernel<<<static_cast<unsigned>(blocks < sms * 8 ? (blocks > 0 ? blocks : 1) : sms * 8), kThreads, 0,

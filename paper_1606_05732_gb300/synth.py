@@ -130,6 +130,9 @@ WORKLOADS = {
     # half the rows of the NMF-like case (CSR 250 MB, still larger than L2), for
     # profiler captures that must stay small
     "nmf_n8M_d64": dict(n=1 << 23, d=64, p=0.05, values="uniform", m=32, B=1 << 17, seed=2),
+    # a quarter of the rows of the precision-ladder case (same B and d, so the same
+    # 134 MB SX), for profiler captures
+    "ladder_n16M_d128": dict(n=1 << 24, d=128, p=0.01, values="normal", m=128, B=1 << 18, seed=3),
     # precision ladder: n=2^26 x d=128, p=0.01, N(0,1); m=128, B=2^18; seed 3
     "ladder_n64M_d128": dict(n=1 << 26, d=128, p=0.01, values="normal", m=128, B=1 << 18, seed=3),
     # differentiation: dense n=2^20 x d=64 (and p=0.02 sparse); m=64, B=2^16; seed 4

@@ -76,6 +76,12 @@ def test_options_and_workspace(lib):
     assert lib.cg_plan_set_option(h, 99, 0) == 1
     assert lib.cg_plan_set_option(h, 3, 12345) == 0
     assert lib.cg_plan_get_option(h, 3, ctypes.byref(val)) == 0 and val.value == 12345
+    for opt, good, bad in [(8, (0, 1, 16), (-1, 17)), (9, (0, 32, 64, 128), (16, 33, 256, -32))]:
+        for x in good:
+            assert lib.cg_plan_set_option(h, opt, x) == 0
+            assert lib.cg_plan_get_option(h, opt, ctypes.byref(val)) == 0 and val.value == x
+        for x in bad:
+            assert lib.cg_plan_set_option(h, opt, x) == 1
     sz = ctypes.c_size_t()
     for op in range(7):
         assert lib.cg_workspace_size(h, op, 1000, ctypes.byref(sz)) == 0

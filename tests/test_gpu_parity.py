@@ -134,6 +134,28 @@ def test_deterministic_mode_is_bit_reproducible_and_exact(n, d, m, B, seed, kind
     assert rel(Y1, Yo) < FP32_TOL
 
 
+@pytest.mark.parametrize("rows", [32, 64, 128])
+@pytest.mark.parametrize("passes", [1, 3])
+@pytest.mark.parametrize("n,d,m,B,seed,kind", [CASES[2], CASES[3], CASES[5], (70001, 128, 16, 5000, 17, "bern0.01")])
+def test_scatter_chunk_rows_and_passes(n, d, m, B, seed, kind, rows, passes):
+    """Every chunk height and bucket-range pass count gives the oracle's SX: the
+    chunk's last row, its ragged tail (n not a multiple of the height) and rows whose
+    buckets fall in each range are all reduced exactly once."""
+    X = make_input(n, d, seed, kind)
+    rp, ci, v = dev_csr(X)
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="atomic", scatter_rows=rows, scatter_passes=passes)
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL
+    det = cg().CountGauss(n, d, m, B, seed, deterministic=True, scatter_rows=rows)
+    SXd = det.sketch_csr(rp, ci, v).cpu().numpy()
+    det.check()
+    assert rel(SXd, SXo) < 1e-6
+
+
 def test_partition_overflow_path():
     """Few, full rows of 4096 entries hashed to 64 slices of 8 buckets: some slice
     receives far more than its share, so its records spill to the overflow list; the
