@@ -328,8 +328,9 @@ def run_ours(args):
     plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter,
                                  scatter_passes=args.scatter_passes, scatter_rows=args.scatter_rows)
     partitioned = args.scatter == "partition"  # auto: the atomic scatter
-    scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_atomic_kernel")
-    scatter_src = ("cg_sketch_part.cu", "cg_rng.cuh") if partitioned else ("cg_sketch.cu", "cg_rng.cuh")
+    scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_kernel")
+    scatter_src = (("cg_sketch_part.cu", "cg_rng.cuh") if partitioned
+                   else ("cg_sketch.cu", "cg_scatter.cuh", "cg_rng.cuh"))
     Y = torch.empty(m, d, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 

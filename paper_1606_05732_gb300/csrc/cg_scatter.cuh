@@ -1,4 +1,4 @@
-// cg_scatter.cuh -- one warp scatters 32 consecutive CSR rows into SX (the O(nnz)
+// cg_scatter.cuh -- one warp scatters a chunk of consecutive CSR rows into SX (the O(nnz)
 // stage of Section 1.1), shared by the scatter kernel and the batched kernel.
 #pragma once
 #include "cg_internal.cuh"
