@@ -4,6 +4,8 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -117,6 +119,29 @@ int num_sms() {
     }
     if (dev < kMaxDevices) g_sms[dev] = sms;
     return sms;
+}
+
+int resident_ctas_per_sm(const void *kernel, int threads, size_t dyn_smem, int tmem_cols) {
+    int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0, blocks_sm = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, kernel) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((fa.numRegs > 0 ? fa.numRegs : 1) * 32 + 255) / 256 * 256;  // 256-register units
+    int n = (regs_sm / regs_warp) / warps;
+    const size_t smem_cta = fa.sharedSizeBytes + dyn_smem + static_cast<size_t>(reserved);
+    if (smem_cta > 0) n = std::min<int>(n, static_cast<int>(static_cast<size_t>(smem_sm) / smem_cta));
+    n = std::min(n, threads_sm / threads);
+    n = std::min(n, blocks_sm);
+    if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
+    return n < 1 ? 1 : n;
 }
 
 cudaError_t launch_generate_words(Key key, uint32_t tag, uint64_t idx0, int64_t count, uint32_t *words,

@@ -80,8 +80,18 @@ int contract_splits(const cg_plan &p) {
     const int TN = p.d > 64 ? 8 : 4;
     const int64_t blocks = static_cast<int64_t>((p.m + kBM - 1) / kBM) * ((p.d + 16 * TN - 1) / (16 * TN));
     const int sms = num_sms() > 0 ? num_sms() : 148;
-    const int64_t target = 3LL * sms;  // about three resident CTAs per SM
-    int64_t s = (target + blocks - 1) / blocks;
+    // whole waves: as many CTAs as fit the GPU at once, never a partial second wave
+    int per_sm = 3;
+    if (num_sms() > 0) {
+        static int resident[2] = {0, 0};
+        int &r = resident[TN == 8 ? 1 : 0];
+        if (r == 0)
+            r = TN == 8 ? resident_ctas_per_sm(reinterpret_cast<const void *>(contract_ffma_kernel<8>), kThreads, 0, 0)
+                        : resident_ctas_per_sm(reinterpret_cast<const void *>(contract_ffma_kernel<4>), kThreads, 0, 0);
+        per_sm = r;
+    }
+    const int64_t target = static_cast<int64_t>(per_sm) * sms;
+    int64_t s = target / blocks;
     s = std::max<int64_t>(1, std::min<int64_t>(s, nslabs));
     return static_cast<int>(s);
 }

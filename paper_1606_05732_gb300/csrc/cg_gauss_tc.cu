@@ -231,8 +231,7 @@ cudaError_t launch_tc(const float *SX, int m, int d, int64_t B, Key key, int nsp
     const int64_t nslabs = (B + kBK - 1) / kBK;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
-    // at least 120 KB of dynamic shared memory: one CTA per SM, so TMEM is never contended
-    const uint32_t smem = C::kSmem > 120u * 1024u ? C::kSmem : 120u * 1024u;
+    const uint32_t smem = C::kSmem;
     cudaError_t e = cudaFuncSetAttribute(contract_tc_bf16_kernel<NT, SPLIT3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -488,7 +487,7 @@ cudaError_t launch_tc8(const float *SX, int m, int d, int64_t B, Key key, int ns
     const int64_t nslabs = (B + kBK8 - 1) / kBK8;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
-    const uint32_t smem = C::kSmem > 120u * 1024u ? C::kSmem : 120u * 1024u;
+    const uint32_t smem = C::kSmem;
     cudaError_t e = cudaFuncSetAttribute(contract_tc_fp8_kernel<NT, SPLIT3>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -501,6 +500,41 @@ cudaError_t launch_tc8(const float *SX, int m, int d, int64_t B, Key key, int ns
 
 int tc8_nt(int d) { return d <= 64 ? 64 : 128; }
 
+// Resident CTAs per SM of each contraction kernel (from its registers, shared memory
+// and TMEM columns; the same on every device of this architecture, so computed once).
+template <int NT, bool SPLIT3>
+int ctas_bf16() {
+    using C = Cfg<NT, SPLIT3>;
+    static int n = 0;
+    if (n == 0)
+        n = resident_ctas_per_sm(reinterpret_cast<const void *>(contract_tc_bf16_kernel<NT, SPLIT3>), kThreads,
+                                 C::kSmem, static_cast<int>(C::kTmemCols));
+    return n;
+}
+
+template <int NT, bool SPLIT3>
+int ctas_fp8() {
+    using C = Cfg8<NT, SPLIT3>;
+    static int n = 0;
+    if (n == 0)
+        n = resident_ctas_per_sm(reinterpret_cast<const void *>(contract_tc_fp8_kernel<NT, SPLIT3>), kThreads,
+                                 C::kSmem, static_cast<int>(C::kTmemCols));
+    return n;
+}
+
+int tc_ctas_per_sm(int precision, int d) {
+    const bool x3 = precision == CG_PREC_BF16X3 || precision == CG_PREC_FP8X3;
+    if (precision == CG_PREC_FP8_E4M3 || precision == CG_PREC_FP8X3) {
+        if (tc8_nt(d) == 64) return x3 ? ctas_fp8<64, true>() : ctas_fp8<64, false>();
+        return x3 ? ctas_fp8<128, true>() : ctas_fp8<128, false>();
+    }
+    switch (tc_nt(d)) {
+        case 64: return x3 ? ctas_bf16<64, true>() : ctas_bf16<64, false>();
+        case 128: return x3 ? ctas_bf16<128, true>() : ctas_bf16<128, false>();
+        default: return x3 ? ctas_bf16<256, true>() : ctas_bf16<256, false>();
+    }
+}
+
 }  // namespace
 
 int contract_tc_splits(const cg_plan &p) {
@@ -511,7 +545,9 @@ int contract_tc_splits(const cg_plan &p) {
     const int nt = fp8 ? tc8_nt(p.d) : tc_nt(p.d);
     const int64_t blocks = static_cast<int64_t>((p.m + kM - 1) / kM) * ((p.d + nt - 1) / nt);
     const int sms = num_sms() > 0 ? num_sms() : 148;
-    int64_t s = (sms + blocks - 1) / blocks;
+    // whole waves: as many CTAs as fit the GPU at once, never a partial second wave
+    const int64_t target = static_cast<int64_t>(sms) * (num_sms() > 0 ? tc_ctas_per_sm(p.precision, p.d) : 1);
+    int64_t s = target / blocks;
     if (s < 1) s = 1;
     if (s > nslabs) s = nslabs;
     return static_cast<int>(s);

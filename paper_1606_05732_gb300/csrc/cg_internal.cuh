@@ -53,6 +53,12 @@ inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255);
 // SM count of the current device (cached per device).  Returns 0 without a device.
 int num_sms();
 
+// Resident CTAs per SM of `kernel` launched with `threads` threads and `dyn_smem` bytes
+// of dynamic shared memory, from its register and shared-memory use and the current
+// device's limits; with tmem_cols > 0 also at most 512 / tmem_cols, so that the TMEM
+// allocations of all resident CTAs fit an SM together.  1 if a query fails.
+int resident_ctas_per_sm(const void *kernel, int threads, size_t dyn_smem, int tmem_cols);
+
 // ---- scatter (cg_sketch.cu) -------------------------------------------------
 cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
