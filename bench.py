@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scatter", choices=["auto", "atomic", "partition"], default="auto")
     ap.add_argument("--scatter-passes", type=int, default=0, help="bucket-range passes of the scatter (0: automatic)")
-    ap.add_argument("--scatter-rows", type=int, default=0, choices=[0, 32, 64, 128],
+    ap.add_argument("--scatter-rows", type=int, default=0, choices=[0, 1, 32, 64, 128],
                     help="CSR rows per warp chunk of the scatter (0: automatic)")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
     return ap.parse_args()

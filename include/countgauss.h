@@ -102,7 +102,9 @@ typedef enum cg_option {
                                  that range of SX in L2); 0 = automatic (one pass), 1..16 forced */
     CG_OPT_SCATTER_ROWS = 9   /* CSR rows per warp chunk of the scatter: 0 = automatic (the
                                  smallest of 32, 64, 128 whose chunk holds about 96 nonzeros on
-                                 average), or 32, 64, 128 forced */
+                                 average), 32, 64, 128 forced (rows staged in shared memory,
+                                 nonzeros swept 32 at a time), or 1 (one row per lane, each
+                                 lane walking its own row) */
 } cg_option;
 
 typedef enum cg_kernel {

@@ -13,16 +13,21 @@ constexpr int kFfmaKT = 32;
 template <int TN>
 struct FfmaShape {
     static constexpr int BN = 16 * TN;
-    static constexpr int kMainFloats = kFfmaKT * (kFfmaBM + BN);
+    static constexpr int kMainFloats = kFfmaKT * (kFfmaBM + 2 * BN);  // G tile + two SX tiles
     static constexpr int kRedFloats = kFfmaThreads * 4 * TN;
     static constexpr int kRawFloats = kMainFloats > kRedFloats ? kMainFloats : kRedFloats;
 };
 
-template <bool COHERENT>
-__device__ __forceinline__ float4 load4(const float4 *p) {
-    if (COHERENT) return __ldcg(p);
-    return __ldg(p);
+// 16-byte asynchronous copy global -> shared through L2 (coherent with writes made
+// earlier in the same launch); `bytes` = 0 fills the 16 bytes with zeros instead.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <bool COHERENT>
 __device__ __forceinline__ float load1(const float *p) {
     if (COHERENT) return __ldcg(p);
@@ -33,17 +38,19 @@ __device__ __forceinline__ float load1(const float *p) {
 //   out[r, c] = sum over b in slabs [s_begin, s_end) x 32 of G[r, b] SX[b, c]
 // for r in [m0, m0 + 64), c in [n0, n0 + 16 TN), written (not accumulated) into the
 // m x d row-major array `out`.  Called by all 256 threads of a CTA; `raw` is the
-// CTA's shared buffer of FfmaShape<TN>::kRawFloats floats.  With COHERENT the SX
-// loads bypass the non-coherent read-only path (SX written earlier in the same launch).
+// CTA's shared buffer of FfmaShape<TN>::kRawFloats floats (16-byte aligned).  With
+// vec_x (d % 4 == 0, SX 16-byte aligned) the SX tile of slab s + 1 is copied with
+// cp.async into the second buffer while slab s's G tile is drawn and multiplied;
+// otherwise it is loaded synchronously (with COHERENT through L2, for SX written
+// earlier in the same launch).
 template <int TN, bool COHERENT>
 __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, int d, int64_t B, Key key,
                                            int64_t s_begin, int64_t s_end, int m0, int n0, bool vec_x,
                                            float *__restrict__ out, float *raw) {
     constexpr int BN = 16 * TN;
-    constexpr int kRawFloats = FfmaShape<TN>::kRawFloats;
-    (void)kRawFloats;
-    float(*sG)[kFfmaBM] = reinterpret_cast<float(*)[kFfmaBM]>(raw);                // [kFfmaKT][kFfmaBM]
-    float(*sX)[BN] = reinterpret_cast<float(*)[BN]>(raw + kFfmaKT * kFfmaBM);      // [kFfmaKT][BN]
+    constexpr int BQ = BN / 4;
+    float(*sG)[kFfmaBM] = reinterpret_cast<float(*)[kFfmaBM]>(raw);  // [kFfmaKT][kFfmaBM]
+    float *sXb = raw + kFfmaKT * kFfmaBM;                              // two [kFfmaKT][BN] tiles
 
     const int bm = min(kFfmaBM, m - m0);
     const int bn = min(BN, d - n0);
@@ -59,6 +66,21 @@ __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, 
     const int tj = tile / mt;
     const uint64_t groups = static_cast<uint64_t>((m + 3) >> 2);
     const int g0 = m0 >> 2;
+    const int gquads = mt * kFfmaKT;
+
+    // SX[b0 .. b0+kFfmaKT, n0 .. n0+bn) of slab sl into tile `buf`, asynchronously.
+    auto stage_x_async = [&](int64_t sl, int buf) {
+        float(*dst)[BN] = reinterpret_cast<float(*)[BN]>(sXb + buf * kFfmaKT * BN);
+        const int64_t b0 = sl * kFfmaKT;
+        for (int q = t; q < kFfmaKT * BQ; q += kFfmaThreads) {
+            const int kk = q / BQ;
+            const int cq = q % BQ;
+            const int64_t b = b0 + kk;
+            const bool in = b < B && 4 * cq < bn;
+            cp_async16(&dst[kk][4 * cq], in ? SX + b * d + n0 + 4 * cq : SX, in ? 16 : 0);
+        }
+        cp_async_commit();
+    };
 
     float acc[4][TN];
 #pragma unroll
@@ -66,29 +88,32 @@ __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, 
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
 
-
-    for (int64_t sl = s_begin; sl < s_end; ++sl) {
+    if (vec_x && s_begin < s_end) stage_x_async(s_begin, 0);
+    int buf = 0;
+    for (int64_t sl = s_begin; sl < s_end; ++sl, buf ^= 1) {
         const int64_t b0 = sl * kFfmaKT;
-        // G[m0 .. m0+4mt, b0 .. b0+kFfmaKT): quads of four rows of one column.
-        for (int q = t; q < mt * kFfmaKT; q += kFfmaThreads) {
-            const int gl = q % mt;
-            const int kk = q / mt;
-            const int64_t b = b0 + kk;
-            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (b < B) z = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(b), static_cast<uint64_t>(g0 + gl));
-            *reinterpret_cast<float4 *>(&sG[kk][4 * gl]) = z;
+        // The other tile was read in the previous slab, before its closing barrier.
+        if (vec_x && sl + 1 < s_end) stage_x_async(sl + 1, buf ^ 1);
+        // G[m0 .. m0+4mt, b0 .. b0+kFfmaKT): quads of four rows of one column, two
+        // independent quads per step.
+        for (int q0 = t; q0 < gquads; q0 += 2 * kFfmaThreads) {
+            const int q1 = q0 + kFfmaThreads;
+            const int kk0 = q0 / mt, kk1 = q1 / mt;
+            const int gl0 = q0 - kk0 * mt, gl1 = q1 - kk1 * mt;
+            float4 z0 = make_float4(0.f, 0.f, 0.f, 0.f), z1 = z0;
+            if (b0 + kk0 < B)
+                z0 = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(b0 + kk0), static_cast<uint64_t>(g0 + gl0));
+            if (q1 < gquads && b0 + kk1 < B)
+                z1 = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(b0 + kk1), static_cast<uint64_t>(g0 + gl1));
+            *reinterpret_cast<float4 *>(&sG[kk0][4 * gl0]) = z0;
+            if (q1 < gquads) *reinterpret_cast<float4 *>(&sG[kk1][4 * gl1]) = z1;
         }
-        // SX[b0 .. b0+kFfmaKT, n0 .. n0+bn)
+        float(*sX)[BN] = reinterpret_cast<float(*)[BN]>(sXb + buf * kFfmaKT * BN);
         if (vec_x) {
-            constexpr int BQ = BN / 4;
-            for (int q = t; q < kFfmaKT * BQ; q += kFfmaThreads) {
-                const int kk = q / BQ;
-                const int cq = q % BQ;
-                const int64_t b = b0 + kk;
-                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (b < B && 4 * cq < bn) x = load4<COHERENT>(reinterpret_cast<const float4 *>(SX + b * d + n0) + cq);
-                *reinterpret_cast<float4 *>(&sX[kk][4 * cq]) = x;
-            }
+            if (sl + 1 < s_end)
+                cp_async_wait<1>();  // this slab's tile has landed (the next may be in flight)
+            else
+                cp_async_wait<0>();
         } else {
             for (int q = t; q < kFfmaKT * BN; q += kFfmaThreads) {
                 const int kk = q / BN;

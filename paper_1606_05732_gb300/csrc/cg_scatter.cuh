@@ -143,6 +143,50 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
     __syncwarp();
 }
 
+// Rows [first, min(first + 32, n)) with one row per lane and no shared memory, for very
+// sparse rows (about two nonzeros or fewer per row): lane l hashes row first + l and, if
+// its bucket lies in [blo, bhi), walks the row's own nonzeros k = row_ptr[i] ..
+// row_ptr[i + 1] - 1, one reduction each.  The warp takes as many steps as its longest
+// row; the lanes' loads of one step fall in the chunk's short, contiguous range of
+// col_idx / vals.  Out-of-range column indices and malformed row offsets are skipped
+// and reported through `bad`.
+template <bool FIXED>
+__device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                                                const float *__restrict__ vals, int first, int n, int d, uint32_t B,
+                                                int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
+                                                int &bad, uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t pol = l2_evict_first_policy();
+    const int i = first + lane;
+    int beg = i < n ? ld_stream_i32(row_ptr + i, pol) : 0;
+    int end = __shfl_down_sync(0xffffffffu, beg, 1);  // row_ptr[i + 1] from the next lane
+    if (i < n) {
+        if (lane == 31 || i + 1 == n) end = __ldg(row_ptr + i + 1);
+        if (beg < 0 || end > nnz || beg > end) {  // malformed row offsets: skip the row
+            bad = 1;
+            end = beg;
+        }
+        uint32_t h;
+        float sg;
+        hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+        if (h < blo || h >= bhi) end = beg;  // another pass reduces this row
+        const size_t base = static_cast<size_t>(h) * d;
+        for (int k = beg; k < end; ++k) {
+            const int j = ld_stream_i32(col_idx + k, pol);
+            const float v = ld_stream_f32(vals + k, pol);
+            if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
+                if (FIXED)
+                    atomicAdd(static_cast<unsigned long long *>(SX) + base + j, to_fixed(sg * v, F));
+                else
+                    atomicAdd(static_cast<float *>(SX) + base + j, sg * v);
+            } else {
+                bad = 1;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // The 32-row chunk (one row per lane).
 template <bool FIXED>
 __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,

@@ -18,42 +18,55 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kUnroll = 4;  // nonzeros in flight per lane
 
-// One warp owns a chunk of ROWS consecutive rows at a time (scatter_chunk): the
-// chunk's rows are hashed by its lanes, its nonzeros are swept with coalesced loads
-// and each becomes one reduction into SX (fp32; with FIXED, int64 fixed point).
+// One warp owns a chunk of consecutive rows at a time: ROWS rows staged in shared
+// memory and swept nonzero by nonzero (scatter_chunk), or, with ROWS = 0, 32 rows of
+// one lane each (scatter_lanes32).  Each nonzero becomes one reduction into SX (fp32;
+// with FIXED, int64 fixed point).
 template <bool FIXED, int ROWS>
 __global__ void __launch_bounds__(kThreads)
 sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
                   int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *__restrict__ SX,
                   const int *__restrict__ maxbits, int *__restrict__ status, uint32_t blo, uint32_t bhi) {
-    __shared__ int s_rp[kWarps][ROWS + 1];
-    __shared__ uint32_t s_h[kWarps][ROWS];
-    __shared__ float s_sg[kWarps][ROWS];
+    constexpr int CH = ROWS == 0 ? 32 : ROWS;
+    __shared__ int s_rp[kWarps][ROWS == 0 ? 1 : ROWS + 1];
+    __shared__ uint32_t s_h[kWarps][CH];
+    __shared__ float s_sg[kWarps][CH];
     const int w = threadIdx.x >> 5;
-    const int nchunks = (n + ROWS - 1) / ROWS;
+    const int nchunks = (n + CH - 1) / CH;
     const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
     int bad = 0;
-    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps)
-        scatter_chunk<FIXED, ROWS>(row_ptr, col_idx, vals, c * ROWS, n, d, B, nnz, key, row_offset, SX, F, s_rp[w],
-                                   s_h[w], s_sg[w], bad, blo, bhi);
+    for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
+        if constexpr (ROWS == 0)
+            scatter_lanes32<FIXED>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, key, row_offset, SX, F, bad, blo,
+                                   bhi);
+        else
+            scatter_chunk<FIXED, ROWS>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, key, row_offset, SX, F,
+                                       s_rp[w], s_h[w], s_sg[w], bad, blo, bhi);
+    }
     if (bad) atomicOr(status, kStatusBounds);
 }
 
-// Rows per warp chunk: `forced` (32, 64 or 128) or, for 0, the smallest height whose
-// chunk holds about 96 nonzeros on average (a few 32-wide sweeps per round trip).
+// Rows per warp chunk: `forced` (1 = one row per lane in chunks of 32, or 32, 64, 128
+// rows staged in shared memory) or, for 0, the smallest staged height whose chunk holds
+// about 96 nonzeros on average.
 int chunk_rows(int n, int nnz, int forced) {
-    if (forced == 32 || forced == 64 || forced == 128) return forced;
+    if (forced == 1 || forced == 32 || forced == 64 || forced == 128) return forced;
     const double per_row = n > 0 ? static_cast<double>(nnz) / n : 0.0;
     if (per_row * 32 >= 96.0) return 32;
     if (per_row * 64 >= 96.0) return 64;
     return 128;
 }
 
+int chunk_height(int rows) { return rows == 1 ? 32 : rows; }
+
 template <bool FIXED>
 void launch_csr_rows(int rows, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
                      const float *vals, int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *SX,
                      const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
-    if (rows == 128)
+    if (rows == 1)
+        sketch_csr_kernel<FIXED, 0><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                   row_offset, SX, maxbits, status, blo, bhi);
+    else if (rows == 128)
         sketch_csr_kernel<FIXED, 128><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
                                                                      row_offset, SX, maxbits, status, blo, bhi);
     else if (rows == 64)
@@ -174,7 +187,7 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
     cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
     if (e != cudaSuccess || n == 0) return e;
     rows = chunk_rows(n, nnz, rows);
-    const int nchunks = (n + rows - 1) / rows;
+    const int nchunks = (n + chunk_height(rows) - 1) / chunk_height(rows);
     const int need = (nchunks + kWarps - 1) / kWarps;
     const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
     record(ev, true, stream);
@@ -212,7 +225,7 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
     if (nnz > 0) absmax_kernel<<<sms * 4, kThreads, 0, stream>>>(vals, nnz, maxbits);
     if (n > 0) {
         rows = chunk_rows(n, nnz, rows);
-        const int nchunks = (n + rows - 1) / rows;
+        const int nchunks = (n + chunk_height(rows) - 1) / chunk_height(rows);
         const int need = (nchunks + kWarps - 1) / kWarps;
         const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
         launch_csr_rows<true>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, acc, maxbits,

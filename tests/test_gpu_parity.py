@@ -134,7 +134,7 @@ def test_deterministic_mode_is_bit_reproducible_and_exact(n, d, m, B, seed, kind
     assert rel(Y1, Yo) < FP32_TOL
 
 
-@pytest.mark.parametrize("rows", [32, 64, 128])
+@pytest.mark.parametrize("rows", [1, 32, 64, 128])
 @pytest.mark.parametrize("passes", [1, 3])
 @pytest.mark.parametrize("n,d,m,B,seed,kind", [CASES[2], CASES[3], CASES[5], (70001, 128, 16, 5000, 17, "bern0.01")])
 def test_scatter_chunk_rows_and_passes(n, d, m, B, seed, kind, rows, passes):
