@@ -38,9 +38,10 @@ WORKLOAD = "nmf_n16M_d64"
 METRIC = "CountGauss nnz(X)/s & HBM-roofline %; speedup vs plain G̃·X, same GB300"
 UNIT = "nnz/s"
 
-# dram bytes (read + write) per launch of the scatter kernel from one ncu capture,
-# keyed by the sha256 of the kernel source it was taken on (null once it changes)
-NCU_TRAFFIC = {}
+# dram bytes (read + write) per launch of the scatter kernel from one ncu capture of the
+# workload named, keyed by the sha256 of the kernel source it was taken on (null once the
+# source changes).  nmf_n16M_d64: 537.88 MB read + 3.67 MB written, captured at full size.
+NCU_TRAFFIC = {("18ae7b3fd2c74695", "nmf_n16M_d64"): 541_555_968}
 
 
 def parse_args():
@@ -52,9 +53,13 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--scatter", choices=["auto", "atomic", "partition"], default="auto")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3", "fp8", "fp8x3"], default="fp32",
+                    help="arithmetic of the Gaussian contraction in the timed step (the scatter is fp32)")
     ap.add_argument("--scatter-passes", type=int, default=0, help="bucket-range passes of the scatter (0: automatic)")
     ap.add_argument("--scatter-rows", type=int, default=0, choices=[0, 1, 32, 64, 128],
                     help="CSR rows per warp chunk of the scatter (0: automatic)")
+    ap.add_argument("--reduction-sweep", action="store_true",
+                    help="instead of the step: random fp32 reduction rate vs array size (the scatter's ceiling)")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
     return ap.parse_args()
 
@@ -219,6 +224,22 @@ def _time_calls(fn, reps, stream, warm=2):
     return a.elapsed_time(b) / reps
 
 
+def reduction_ceiling(dev, count, cells, reps=5):
+    """Random fp32 reductions per second on this GPU: cg_diag_random_reductions adds 1.0
+    at `count` hashed positions of a `cells`-float array (the SX size) with the scatter
+    kernel's grid, no loads -- one reduction per nonzero is all the scatter must issue,
+    so this rate bounds it from above the way the copy bandwidth bounds a stream."""
+    import torch
+
+    from paper_1606_05732_gb300 import countgauss
+    acc = torch.zeros(cells, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ms = _time_calls(lambda: countgauss.diag_random_reductions(acc, count), reps, stream)
+    del acc
+    return {"per_s": count / (ms / 1e3), "ms": ms, "count": count, "array_bytes": 4 * cells,
+            "how": "cg_diag_random_reductions: count fp32 adds at hashed positions of an SX-sized array"}
+
+
 def measure_rows(dev, reps):
     """The other rows of the hot path, each on its own workload (sizes in synth.WORKLOADS):
     precision ladder and plain product on the largest workload, dense forward and
@@ -325,7 +346,7 @@ def run_ours(args):
     ci_h = torch.from_numpy(X.col_idx).pin_memory()
     v_h = torch.from_numpy(X.vals).pin_memory()
     rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
-    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter,
+    plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter, precision=args.precision,
                                  scatter_passes=args.scatter_passes, scatter_rows=args.scatter_rows)
     partitioned = args.scatter == "partition"  # auto: the atomic scatter
     scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_kernel")
@@ -376,7 +397,8 @@ def run_ours(args):
     sketch_avg_s = (sketch_ms / max(1, sketch_n)) / 1e3
     achieved = alg_bytes / sketch_avg_s / 1e9
     src = source_hash(*scatter_src)
-    traffic = NCU_TRAFFIC.get(src)
+    traffic = NCU_TRAFFIC.get((src, args.workload)) if not partitioned else None
+    red_ceiling = reduction_ceiling(dev, nnz, B * d) if rank == 0 else None
 
     # plain G~.X on the same input
     plain_steps = max(3, args.steps // 4)
@@ -455,14 +477,19 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else f"f32+{args.precision}",
+            "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": d, "p": wl["p"], "values": wl["values"],
                        "nnz_per_rank": nnz, "m": m, "B": B, "seed": seed,
                        "l2": "CSR inputs (%.0f MB) exceed L2; no flush" % (h2d / 1e6)},
             "roofline": {"kernel": scatter_kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sketch_avg_s * 1e3,
-                         "launches": sketch_n},
+                         "launches": sketch_n,
+                         "reduction_bound": None if red_ceiling is None else {
+                             "reductions_per_launch": nnz, "achieved_per_s": nnz / sketch_avg_s,
+                             "ceiling_per_s": red_ceiling["per_s"],
+                             "frac": (nnz / sketch_avg_s) / red_ceiling["per_s"], "ceiling": red_ceiling}},
             "stages_ms": {"sketch_kernel": sketch_ms / max(1, sketch_n),
                           "contract_kernel": contract_ms / max(1, contract_n)},
             "plain": {"ms_per_step": plain_ms, "value": world * nnz / (plain_ms / 1e3), "unit": UNIT,
@@ -480,9 +507,27 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def reduction_sweep():
+    """One JSON line: random fp32 reductions per second (cg_diag_random_reductions, 50 M
+    adds) into arrays from 8 MB to 256 MB -- where the L2 stops holding the array the
+    rate falls, which is the ceiling of the scatter for an SX of that size."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    count = 50_000_000
+    out = []
+    for mb in (8, 16, 32, 48, 64, 80, 96, 112, 128, 134, 160, 192, 256):
+        cells = (mb << 20) // 4
+        r = reduction_ceiling(dev, count, cells)
+        out.append({"array_mb": mb, "reductions_per_s": r["per_s"], "ms": r["ms"]})
+    print(json.dumps({"reduction_sweep": out, "count": count}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.reduction_sweep:
+        reduction_sweep()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

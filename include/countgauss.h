@@ -331,6 +331,19 @@ CG_API cg_status cg_generate_hash_sign(uint64_t seed, int64_t B, int64_t row0, i
 CG_API cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r0, int64_t r1,
                                int64_t c0, int64_t c1, float *out, void *stream);
 
+/* ---- diagnostics ----------------------------------------------------------------
+ * No counterpart in the paper.  The CSR scatter makes one fp32 reduction into SX per
+ * nonzero, so on a GPU whose L2 reduction rate is below what its memory bandwidth
+ * could feed, that rate and not HBM bandwidth bounds the scatter.  This call measures
+ * the bound: it adds 1.0f at `count` pseudo-random positions of `array` (device,
+ * `cells` floats, 4-byte aligned; position of the k-th add = lowbias32(k) mod cells,
+ * lowbias32 being C. Wellons' 32-bit integer hash) with the scatter kernel's grid and
+ * block shape, asynchronously on `stream`; time it with events around the call.  The
+ * sum of `array` grows by exactly `count` (each cell stays an exact integer below
+ * 2^24).  Errors: CG_ERR_INVALID_ARG for a null or misaligned array, cells < 1 or
+ * cells >= 2^32, count < 0 or count >= 2^32. */
+CG_API cg_status cg_diag_random_reductions(float *array, int64_t cells, int64_t count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

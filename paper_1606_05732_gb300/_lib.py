@@ -61,6 +61,7 @@ SIGNATURES = {
     "cg_generate_words": [U64, U32, U64, I64, P, P],
     "cg_generate_hash_sign": [U64, I64, I64, I64, P, P, P],
     "cg_generate_gaussian": [U64, U32, I64, I64, I64, I64, I64, P, P],
+    "cg_diag_random_reductions": [P, I64, I64, P],
 }
 
 

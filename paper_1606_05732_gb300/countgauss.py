@@ -331,6 +331,14 @@ def generate_gaussian(seed: int, tag: int, R: int, r0: int, r1: int, c0: int, c1
     return out
 
 
+def diag_random_reductions(array, count: int):
+    """Add 1.0 at `count` hashed positions of the float32 device tensor `array`
+    (cg_diag_random_reductions: the reduction-rate ceiling of the scatter)."""
+    array = _need(array, torch.float32, "array")
+    _lib.call("cg_diag_random_reductions", _ptr(array), array.numel(), int(count), _stream(array.device))
+    return array
+
+
 # -- autograd ---------------------------------------------------------------------
 class CountGaussDenseFn(torch.autograd.Function):
     """Y = T.X for dense X; backward dX = T^T dY = S^T (G^T dY) with G regenerated."""

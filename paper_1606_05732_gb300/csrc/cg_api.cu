@@ -98,6 +98,24 @@ __global__ void generate_gaussian_kernel(Key key, uint32_t tag, int64_t R, int64
     }
 }
 
+// lowbias32 (C. Wellons): a 32-bit integer hash with good avalanche, used only to
+// spread the diagnostic's reductions over the array.
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// `count` reductions of 1.0f at lowbias32(k) mod cells, grid-stride over k, with the
+// scatter kernel's block size (256) and grid.
+__global__ void __launch_bounds__(256) random_reductions_kernel(float *__restrict__ a, uint32_t cells, uint32_t count) {
+    for (uint32_t k = blockIdx.x * 256u + threadIdx.x; k < count; k += gridDim.x * 256u)
+        atomicAdd(a + lowbias32(k) % cells, 1.0f);
+}
+
 unsigned dump_grid(int64_t count) {
     const int64_t g = (count + 255) / 256;
     return static_cast<unsigned>(g < 1 ? 1 : (g > 65536 ? 65536 : g));
@@ -572,6 +590,16 @@ cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r
     if ((r1 - r0) * (c1 - c0) > 0 && out == nullptr) return CG_ERR_INVALID_ARG;
     if ((r1 - r0) * (c1 - c0) == 0) return CG_OK;
     return from_cuda(launch_generate_gaussian(make_key(seed), tag, R, r0, r1, c0, c1, out, as_stream(stream)));
+}
+
+cg_status cg_diag_random_reductions(float *array, int64_t cells, int64_t count, void *stream) {
+    if (array == nullptr || misaligned(array, 4) || cells < 1 || cells >= (1LL << 32) || count < 0 ||
+        count >= (1LL << 32))
+        return CG_ERR_INVALID_ARG;
+    if (count == 0) return CG_OK;
+    random_reductions_kernel<<<sketch_default_ctas(), 256, 0, as_stream(stream)>>>(
+        array, static_cast<uint32_t>(cells), static_cast<uint32_t>(count));
+    return from_cuda(cudaGetLastError());
 }
 
 }  // extern "C"

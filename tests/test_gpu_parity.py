@@ -325,3 +325,17 @@ def test_argument_errors_raise():
     rp = torch.zeros(11, dtype=torch.int64, device="cuda")
     with pytest.raises(TypeError):
         plan.apply_csr(rp, rp.int(), torch.zeros(0, device="cuda"))
+
+
+def test_diag_random_reductions_adds_exactly_count():
+    """The reduction-rate diagnostic adds 1.0 exactly `count` times (each cell stays an
+    exact integer), and spreads the adds over the whole array."""
+    a = torch.zeros(100003, device="cuda")
+    cg().diag_random_reductions(a, 3_000_000)
+    h = a.cpu().numpy().astype(np.float64)
+    assert h.sum() == 3_000_000
+    assert (h == np.round(h)).all()
+    assert (h > 0).mean() > 0.99
+    from paper_1606_05732_gb300 import _lib
+    with pytest.raises(_lib.CountGaussError):
+        cg().diag_random_reductions(a, -1)
