@@ -15,7 +15,8 @@ Printed JSON line (rank 0):
                  (8 nnz + 4 (n+1) + 4 B d) over its CUDA-event duration, against the
                  measured HBM copy bandwidth
   plain          the plain G~.X on the same input and GPU, and the speedup over it
-  e2e            the same metric with the CSR copied host->device and Y read back
+  e2e            the same metric through cg_apply_csr_host: the CSR in pinned host memory,
+                 copied host->device in chunks that overlap the scatter, Y read back
                  every step, through the same public call
   cpu_baseline   the FP64 oracle on this machine's host cores (rank 0, N = 1)
 
@@ -58,9 +59,13 @@ def parse_args():
     ap.add_argument("--scatter-passes", type=int, default=0, help="bucket-range passes of the scatter (0: automatic)")
     ap.add_argument("--scatter-rows", type=int, default=0, choices=[0, 1, 32, 64, 128],
                     help="CSR rows per warp chunk of the scatter (0: automatic)")
+    ap.add_argument("--host-chunk", type=int, default=0,
+                    help="nonzeros per chunk of the end-to-end host-input call (0: automatic)")
     ap.add_argument("--reduction-sweep", action="store_true",
                     help="instead of the step: random fp32 reduction rate vs array size (the scatter's ceiling)")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
+    ap.add_argument("--rows", default="ladder,grad,batch,small",
+                    help="comma list of the other rows to measure (ladder, grad, batch, small)")
     return ap.parse_args()
 
 
@@ -240,14 +245,12 @@ def reduction_ceiling(dev, count, cells, reps=5):
             "how": "cg_diag_random_reductions: count fp32 adds at hashed positions of an SX-sized array"}
 
 
-def measure_rows(dev, reps):
+def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small")):
     """The other rows of the hot path, each on its own workload (sizes in synth.WORKLOADS):
     precision ladder and plain product on the largest workload, dense forward and
     adjoint, the 96-instance batch, deterministic mode, and the small case's latency."""
     import numpy as np
     import torch
-
-    from paper_1606_05732_gb300 import _lib, countgauss, synth
 
     stream = torch.cuda.current_stream(dev)
     rows = {}
@@ -256,7 +259,23 @@ def measure_rows(dev, reps):
         return (torch.from_numpy(X.row_ptr.astype(np.int32)).to(dev), torch.from_numpy(X.col_idx).to(dev),
                 torch.from_numpy(X.vals).to(dev))
 
-    # precision ladder + plain product at the largest workload
+    if "ladder" in which:
+        rows.update(_ladder_row(dev, reps, csr_dev, stream))
+    if "grad" in which:
+        rows.update(_grad_row(dev, reps, csr_dev, stream))
+    if "batch" in which:
+        rows.update(_batch_row(dev, reps, csr_dev, stream))
+    if "small" in which:
+        rows.update(_small_row(dev, reps, csr_dev, stream))
+    return rows
+
+
+def _ladder_row(dev, reps, csr_dev, stream):
+    """Every precision of the contraction, and the plain product, at the largest workload."""
+    import torch
+
+    from paper_1606_05732_gb300 import _lib, countgauss, synth
+    rows = {}
     X, w = synth.workload_csr("ladder_n64M_d128")
     rp, ci, v = csr_dev(X)
     ladder = {}
@@ -279,8 +298,15 @@ def measure_rows(dev, reps):
                                 "plain_ms": plain_ms,
                                 "speedup_fp32_over_plain": plain_ms / ladder["fp32"]["ms_per_call"]}
     del rp, ci, v, X
+    return rows
 
-    # dense forward and adjoint (dense and at the stored entries of the p = 0.02 variant)
+
+def _grad_row(dev, reps, csr_dev, stream):
+    """Dense forward and adjoint (dense, and at the stored entries of the p = 0.02 variant)."""
+    import torch
+
+    from paper_1606_05732_gb300 import countgauss, synth
+    rows = {}
     w = synth.WORKLOADS["grad_n1M_d64"]
     Xd = torch.from_numpy(synth.dense_normal(w["n"], w["d"], seed=w["seed"])).to(dev)
     Xs = synth.csr_bernoulli(w["n"], w["d"], w["p"], seed=w["seed"])
@@ -295,8 +321,13 @@ def measure_rows(dev, reps):
                             "adjoint_dense_ms": bwd, "adjoint_dense_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / bwd / 1e6,
                             "adjoint_csr_ms": bwd_s, "adjoint_csr_nnz": Xs.nnz}
     del Xd, rp, ci, v
+    return rows
 
-    # the 96-instance batch, autotuned, replayed from a CUDA graph
+
+def _batch_row(dev, reps, csr_dev, stream):
+    """The 96-instance batch, autotuned, replayed from a CUDA graph."""
+    from paper_1606_05732_gb300 import _lib, countgauss, synth
+    rows = {}
     params = synth.batch_instances()
     Xs = synth.batch_inputs(params)
     insts = []
@@ -313,13 +344,47 @@ def measure_rows(dev, reps):
                                   "contract_fma": batch.get_option(_lib.BATCH_OPT_CONTRACT_FMA),
                                   "ctas_per_sm": batch.get_option(_lib.BATCH_OPT_CTAS_PER_SM)}}
     del insts, batch
+    return rows
 
-    # small case latency
+
+def _graph_us(fn, reps, dev, per_graph=10):
+    """Device time per call of fn (us): `per_graph` calls captured once in a CUDA graph and
+    replayed, so that the Python call overhead is not in the measurement."""
+    import torch
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            fn()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(per_graph):
+            fn()
+    ms = _time_calls(g.replay, reps, torch.cuda.current_stream(dev))
+    del g
+    return 1e3 * ms / per_graph
+
+
+def _small_row(dev, reps, csr_dev, stream):
+    """Latency of the small case, CountGauss and plain: device time per call (calls
+    replayed from a CUDA graph) and the time of a call from Python."""
+    import torch
+
+    from paper_1606_05732_gb300 import countgauss, synth
+    rows = {}
     X, w = synth.workload_csr("small_n65536_d16")
     rp, ci, v = csr_dev(X)
     plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"])
-    rows["small_n65536_d16"] = {"apply_csr_us": 1e3 * _time_calls(lambda: plan.apply_csr(rp, ci, v), reps, stream),
-                                "plain_us": 1e3 * _time_calls(lambda: plan.plain_csr(rp, ci, v), reps, stream)}
+    Y = torch.empty(w["m"], w["d"], dtype=torch.float32, device=dev)
+    Yp = torch.empty_like(Y)
+    rows["small_n65536_d16"] = {
+        "apply_csr_us": _graph_us(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, dev),
+        "plain_us": _graph_us(lambda: plan.plain_csr(rp, ci, v, out=Yp), reps, dev),
+        "apply_csr_python_call_us": 1e3 * _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, stream),
+        "plain_python_call_us": 1e3 * _time_calls(lambda: plan.plain_csr(rp, ci, v, out=Yp), reps, stream)}
+    plan.check()
     return rows
 
 
@@ -421,18 +486,18 @@ def run_ours(args):
     det_plan.check()
     del det_plan
 
-    # end to end through the same call: H2D of the CSR, apply, D2H of Y, every step
-    rp2, ci2, v2 = torch.empty_like(rp), torch.empty_like(ci), torch.empty_like(v)
+    # end to end through the host-input call: H2D of the CSR, apply, D2H of Y, every step
+    # (cg_apply_csr_host: the CSR in pinned host memory is copied in chunks on a second
+    # stream while earlier chunks are scattered; Y comes back to host memory)
     Y_h = torch.empty(m, d, dtype=torch.float32).pin_memory()
+    plan.set_host_chunk(args.host_chunk)
 
     def e2e_step():
-        rp2.copy_(rp_h, non_blocking=True)
-        ci2.copy_(ci_h, non_blocking=True)
-        v2.copy_(v_h, non_blocking=True)
-        plan.apply_csr(rp2, ci2, v2, out=Y)
+        plan.apply_csr_host(rp_h, ci_h, v_h, out=Y_h, device=dev)
         if pg is not None:
+            Y.copy_(Y_h, non_blocking=True)
             pg.all_reduce(Y)
-        Y_h.copy_(Y, non_blocking=True)
+            Y_h.copy_(Y, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -454,9 +519,8 @@ def run_ours(args):
 
     rows = None
     if rank == 0 and world == 1 and not args.no_rows:
-        del rp2, ci2, v2
         torch.cuda.empty_cache()
-        rows = measure_rows(dev, max(5, args.steps // 10))
+        rows = measure_rows(dev, max(5, args.steps // 10), tuple(args.rows.split(",")))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -495,7 +559,7 @@ def run_ours(args):
             "plain": {"ms_per_step": plain_ms, "value": world * nnz / (plain_ms / 1e3), "unit": UNIT,
                       "speedup_countgauss_over_plain": plain_ms / ms_step},
             "e2e": {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "cg_apply_csr_host"},
             "gpu_launches": 3 * args.steps,
             "clocks": clk.summary(),
             "deterministic": {"ms_per_step": det_ms, "value": world * nnz / (det_ms / 1e3), "unit": UNIT},

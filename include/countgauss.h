@@ -100,11 +100,13 @@ typedef enum cg_option {
     CG_OPT_SCATTER_PASSES = 8, /* bucket-range passes of the atomic CSR scatter (each pass streams
                                  the CSR and reduces the rows of one range of buckets, keeping
                                  that range of SX in L2); 0 = automatic (one pass), 1..16 forced */
-    CG_OPT_SCATTER_ROWS = 9   /* CSR rows per warp chunk of the scatter: 0 = automatic (the
+    CG_OPT_SCATTER_ROWS = 9,  /* CSR rows per warp chunk of the scatter: 0 = automatic (the
                                  smallest of 32, 64, 128 whose chunk holds about 96 nonzeros on
                                  average), 32, 64, 128 forced (rows staged in shared memory,
                                  nonzeros swept 32 at a time), or 1 (one row per lane, each
                                  lane walking its own row) */
+    CG_OPT_HOST_CHUNK = 10    /* cg_apply_csr_host: most nonzeros, and most rows, per chunk copied
+                                 to the device; 0 = automatic (2^22), else 32 .. 2^30 */
 } cg_option;
 
 typedef enum cg_kernel {
@@ -123,7 +125,8 @@ typedef enum cg_op {
     CG_OP_ADJOINT_CSR = 3,
     CG_OP_PLAIN_CSR = 4,
     CG_OP_SKETCH = 5,         /* cg_sketch_csr / cg_sketch_dense alone */
-    CG_OP_CONTRACT = 6        /* cg_contract alone */
+    CG_OP_CONTRACT = 6,       /* cg_contract alone */
+    CG_OP_APPLY_CSR_HOST = 7  /* cg_apply_csr_host */
 } cg_op;
 
 /* ---- plans ---------------------------------------------------------------- */
@@ -330,6 +333,28 @@ CG_API cg_status cg_generate_hash_sign(uint64_t seed, int64_t B, int64_t row0, i
  * Box-Muller the kernels use. */
 CG_API cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r0, int64_t r1,
                                int64_t c0, int64_t c1, float *out, void *stream);
+
+/* Y = T.X (as cg_apply_csr) for a CSR X held in HOST memory, with Y written to HOST
+ * memory: the end-to-end form, for callers whose data live on the host.  The rows are
+ * cut into chunks of at most CG_OPT_HOST_CHUNK nonzeros and rows (boundaries found by
+ * binary search on the host row_ptr before anything is enqueued); an internal copy
+ * stream copies chunk c + 1 into one of two staging buffers of the workspace while chunk
+ * c is scattered on `stream`, then the contraction runs on `stream` and Y (m x d, row-
+ * major) is copied back.  Pinned (page-locked) host memory lets the copies overlap the
+ * scatter; pageable memory works but its copies are not asynchronous.  The call returns
+ * after enqueueing: Y is valid, and the host arrays may be changed or freed, once
+ * `stream` has reached the end of the call (e.g. after cudaStreamSynchronize).
+ * row_ptr (n + 1 entries, read by the host during the call), col_idx, vals (nnz entries
+ * each): host pointers.  ws: device workspace of cg_workspace_size(plan,
+ * CG_OP_APPLY_CSR_HOST, nnz) bytes.  Errors: CG_ERR_INVALID_ARG for null or misaligned
+ * pointers or row offsets outside [0, nnz] at a chunk boundary (offsets inside a chunk
+ * are checked on the device, as in cg_apply_csr); CG_ERR_UNSUPPORTED for a
+ * deterministic plan, the partitioned scatter, or a row with more nonzeros than the
+ * chunk size.  Paper: Section 1.1 (the transform); the chunking is an implementation
+ * matter with no counterpart in the paper. */
+CG_API cg_status cg_apply_csr_host(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
+                                   const float *vals, int64_t nnz, float *Y, void *ws, size_t ws_bytes,
+                                   void *stream);
 
 /* ---- diagnostics ----------------------------------------------------------------
  * No counterpart in the paper.  The CSR scatter makes one fp32 reduction into SX per

@@ -26,6 +26,8 @@ OPT_SCATTER, OPT_SCATTER_PASSES, OPT_SCATTER_ROWS = 7, 8, 9
 SCATTER = {"auto": 0, "atomic": 1, "partition": 2}
 KERNEL_SKETCH, KERNEL_CONTRACT, KERNEL_PLAIN, KERNEL_ADJOINT_W, KERNEL_GATHER = range(5)
 OP_APPLY_CSR, OP_APPLY_DENSE, OP_ADJOINT_DENSE, OP_ADJOINT_CSR, OP_PLAIN_CSR, OP_SKETCH, OP_CONTRACT = range(7)
+OP_APPLY_CSR_HOST = 7
+OPT_HOST_CHUNK = 10
 
 P = ctypes.c_void_p
 I32, I64, U32, U64, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
@@ -40,6 +42,7 @@ SIGNATURES = {
     "cg_plan_check": [P, P, P],
     "cg_plan_timing": [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
     "cg_apply_csr": [P, P, P, P, I64, P, P, SZ, P],
+    "cg_apply_csr_host": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_csr_noalloc": [P, P, P, P, I64, P, P],
     "cg_apply_dense": [P, P, I64, P, P, SZ, P],
     "cg_apply_adjoint": [P, P, P, P, I64, P, P, SZ, P],

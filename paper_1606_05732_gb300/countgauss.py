@@ -31,6 +31,18 @@ def _stream(device) -> _P:
     return _P(torch.cuda.current_stream(device).cuda_stream)
 
 
+def _need_host(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cpu":
+        raise ValueError(f"{name} must be a CPU tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
 def _need(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch.Tensor")
@@ -123,6 +135,31 @@ class CountGauss:
         _lib.check("cg_apply_csr", self._lib.cg_apply_csr(
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
         return Y
+
+    def apply_csr_host(self, row_ptr, col_idx, vals, out=None, device=None) -> torch.Tensor:
+        """Y = G.(S.X) for a CSR X in host memory, Y returned in host memory
+        (cg_apply_csr_host: chunked copies on a second stream overlap the scatter).
+        Pinned CPU tensors make the copies asynchronous.  Synchronises the device's
+        current stream before returning, so Y is ready."""
+        row_ptr = _need_host(row_ptr, torch.int32, "row_ptr")
+        col_idx = _need_host(col_idx, torch.int32, "col_idx")
+        vals = _need_host(vals, torch.float32, "vals")
+        if row_ptr.numel() != self.n + 1:
+            raise ValueError(f"row_ptr must have n + 1 = {self.n + 1} entries")
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        nnz = col_idx.numel()
+        Y = torch.empty(self.m, self.d, dtype=torch.float32, pin_memory=True) if out is None else out
+        if Y.device.type != "cpu" or not Y.is_contiguous() or Y.dtype != torch.float32:
+            raise ValueError("out must be a contiguous float32 CPU tensor")
+        ws = self.workspace(_lib.OP_APPLY_CSR_HOST, nnz, dev)
+        _lib.check("cg_apply_csr_host", self._lib.cg_apply_csr_host(
+            self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
+        torch.cuda.current_stream(dev).synchronize()
+        return Y
+
+    def set_host_chunk(self, nnz_per_chunk: int) -> None:
+        """Most nonzeros and rows per chunk of apply_csr_host (CG_OPT_HOST_CHUNK; 0: automatic)."""
+        self.set_option(_lib.OPT_HOST_CHUNK, int(nnz_per_chunk))
 
     def apply_dense(self, X, out=None) -> torch.Tensor:
         """Y = G.(S.X) for dense row-major X (n x d)."""

@@ -224,6 +224,25 @@ struct Layout {
     PartLayout part;
 };
 
+// Chunk sizes of cg_apply_csr_host and the bytes of one staging buffer (row offsets,
+// column indices, values of one chunk, each 256-aligned).
+struct HostCaps {
+    int64_t nnz = 1, rows = 1;
+    size_t rp_off = 0, ci_off = 0, v_off = 0, stage_bytes = 0;
+};
+
+HostCaps host_caps(const cg_plan &p, int64_t nnz) {
+    HostCaps c;
+    const int64_t chunk = p.host_chunk > 0 ? p.host_chunk : (1LL << 22);
+    c.nnz = std::max<int64_t>(1, std::min(nnz, chunk));
+    c.rows = std::max<int64_t>(1, std::min(p.n, chunk));
+    c.rp_off = 0;
+    c.ci_off = align256(static_cast<size_t>(c.rows + 1) * sizeof(int32_t));
+    c.v_off = c.ci_off + align256(static_cast<size_t>(c.nnz) * sizeof(int32_t));
+    c.stage_bytes = c.v_off + align256(static_cast<size_t>(c.nnz) * sizeof(float));
+    return c;
+}
+
 Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
     Layout L;
     const size_t sx = static_cast<size_t>(p.B) * p.d * sizeof(float);
@@ -250,6 +269,13 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
         case CG_OP_SKETCH:
             L.c_bytes = scatter_scratch(p, nnz, &L.part);
             break;
+        case CG_OP_APPLY_CSR_HOST: {
+            const HostCaps c = host_caps(p, nnz);
+            L.a_bytes = sx;
+            L.b_bytes = contract_partials_bytes(p);
+            L.c_bytes = 2 * c.stage_bytes + static_cast<size_t>(p.m) * p.d * sizeof(float);
+            break;
+        }
         default:
             break;
     }
@@ -310,6 +336,49 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
                                               p->scatter_passes, p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st));
 }
 
+// Copy stream and events of cg_apply_csr_host, made on first use on a device and kept
+// by the plan (remade if the plan is used on another device).
+struct HostState {
+    int device = -1;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t start = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t consumed[2] = {nullptr, nullptr};
+};
+
+void destroy_host_state(cg_plan *p) {
+    HostState *h = static_cast<HostState *>(p->host_state);
+    if (h == nullptr) return;
+    if (h->copy != nullptr) cudaStreamDestroy(h->copy);
+    for (cudaEvent_t e : {h->start, h->copied[0], h->copied[1], h->consumed[0], h->consumed[1]})
+        if (e != nullptr) cudaEventDestroy(e);
+    delete h;
+    p->host_state = nullptr;
+}
+
+HostState *host_state(cg_plan *p) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    HostState *h = static_cast<HostState *>(p->host_state);
+    if (h != nullptr && h->device == dev) return h;
+    destroy_host_state(p);
+    h = new (std::nothrow) HostState;
+    if (h == nullptr) return nullptr;
+    h->device = dev;
+    p->host_state = h;
+    bool ok = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaEventCreateWithFlags(&h->copied[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->consumed[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        destroy_host_state(p);
+        return nullptr;
+    }
+    return h;
+}
+
 }  // namespace
 
 extern "C" {
@@ -351,6 +420,8 @@ cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t se
     p->scatter = 0;
     p->scatter_passes = 0;
     p->scatter_rows = 0;
+    p->host_chunk = 0;
+    p->host_state = nullptr;
     *out = p;
     return CG_OK;
 }
@@ -368,6 +439,7 @@ cg_status cg_plan_destroy(cg_plan *plan) {
         }
         delete ts;
     }
+    destroy_host_state(plan);
     delete plan;
     return CG_OK;
 }
@@ -426,6 +498,10 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             if (value != 0 && value != 1 && value != 32 && value != 64 && value != 128) return CG_ERR_INVALID_ARG;
             p->scatter_rows = static_cast<int32_t>(value);
             return CG_OK;
+        case CG_OPT_HOST_CHUNK:
+            if (value != 0 && (value < 32 || value > (1LL << 30))) return CG_ERR_INVALID_ARG;
+            p->host_chunk = value;
+            return CG_OK;
         default:
             return CG_ERR_INVALID_ARG;
     }
@@ -443,12 +519,13 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
         case CG_OPT_SCATTER: *value = p->scatter; return CG_OK;
         case CG_OPT_SCATTER_PASSES: *value = p->scatter_passes; return CG_OK;
         case CG_OPT_SCATTER_ROWS: *value = p->scatter_rows; return CG_OK;
+        case CG_OPT_HOST_CHUNK: *value = p->host_chunk; return CG_OK;
         default: return CG_ERR_INVALID_ARG;
     }
 }
 
 cg_status cg_workspace_size(const cg_plan *p, int32_t op, int64_t nnz, size_t *bytes) {
-    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_CONTRACT) return CG_ERR_INVALID_ARG;
+    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_APPLY_CSR_HOST) return CG_ERR_INVALID_ARG;
     *bytes = layout_for(*p, op, nnz).total;
     return CG_OK;
 }
@@ -590,6 +667,77 @@ cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r
     if ((r1 - r0) * (c1 - c0) > 0 && out == nullptr) return CG_ERR_INVALID_ARG;
     if ((r1 - r0) * (c1 - c0) == 0) return CG_OK;
     return from_cuda(launch_generate_gaussian(make_key(seed), tag, R, r0, r1, c0, c1, out, as_stream(stream)));
+}
+
+cg_status cg_apply_csr_host(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                            int64_t nnz, float *Y, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
+    if (s != CG_OK) return s;
+    if (p->deterministic || use_partition(*p)) return CG_ERR_UNSUPPORTED;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_APPLY_CSR_HOST, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    const HostCaps caps = host_caps(*p, nnz);
+    const int64_t n = p->n;
+    // Chunk boundaries [r0, r1): the most rows (at most caps.rows) whose nonzeros
+    // row_ptr[r0] .. row_ptr[r1] number at most caps.nnz, by binary search.
+    std::vector<int64_t> cuts{0};
+    if (row_ptr[0] < 0 || row_ptr[n] > nnz || row_ptr[0] > row_ptr[n]) return CG_ERR_INVALID_ARG;
+    for (int64_t r0 = 0; r0 < n;) {
+        const int64_t k0 = row_ptr[r0];
+        auto fits = [&](int64_t r) { return row_ptr[r] >= k0 && row_ptr[r] - k0 <= caps.nnz && row_ptr[r] <= nnz; };
+        int64_t lo = r0 + 1, hi = std::min(n, r0 + caps.rows);
+        if (!fits(lo)) return row_ptr[lo] < k0 || row_ptr[lo] > nnz ? CG_ERR_INVALID_ARG : CG_ERR_UNSUPPORTED;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo + 1) / 2;
+            if (fits(mid)) lo = mid; else hi = mid - 1;
+        }
+        cuts.push_back(lo);
+        r0 = lo;
+    }
+    HostState *h = host_state(p);
+    if (h == nullptr) return CG_ERR_CUDA;
+    cudaStream_t st = as_stream(stream);
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    char *stage0 = region(ws, L.c_off);
+    float *Yd = reinterpret_cast<float *>(stage0 + 2 * caps.stage_bytes);
+    const Key key = make_key(p->seed);
+    if (cudaMemsetAsync(SX, 0, static_cast<size_t>(p->B) * p->d * sizeof(float), st) != cudaSuccess) return CG_ERR_CUDA;
+    // The copies start after earlier work on `stream` and after the staging buffers'
+    // last readers (a previous call, possibly on another stream).
+    if (cudaEventRecord(h->start, st) != cudaSuccess || cudaStreamWaitEvent(h->copy, h->start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(h->copy, h->consumed[0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(h->copy, h->consumed[1], 0) != cudaSuccess)
+        return CG_ERR_CUDA;
+    for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+        const int b = static_cast<int>(c & 1);
+        const int64_t r0 = cuts[c], r1 = cuts[c + 1];
+        const int64_t k0 = row_ptr[r0], k1 = row_ptr[r1];
+        char *stage = stage0 + b * caps.stage_bytes;
+        int32_t *rp = reinterpret_cast<int32_t *>(stage + caps.rp_off);
+        int32_t *ci = reinterpret_cast<int32_t *>(stage + caps.ci_off);
+        float *v = reinterpret_cast<float *>(stage + caps.v_off);
+        if (c >= 2 && cudaStreamWaitEvent(h->copy, h->consumed[b], 0) != cudaSuccess) return CG_ERR_CUDA;
+        if (cudaMemcpyAsync(rp, row_ptr + r0, static_cast<size_t>(r1 - r0 + 1) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, h->copy) != cudaSuccess)
+            return CG_ERR_CUDA;
+        if (k1 > k0 && (cudaMemcpyAsync(ci, col_idx + k0, static_cast<size_t>(k1 - k0) * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice, h->copy) != cudaSuccess ||
+                        cudaMemcpyAsync(v, vals + k0, static_cast<size_t>(k1 - k0) * sizeof(float),
+                                        cudaMemcpyHostToDevice, h->copy) != cudaSuccess))
+            return CG_ERR_CUDA;
+        if (cudaEventRecord(h->copied[b], h->copy) != cudaSuccess || cudaStreamWaitEvent(st, h->copied[b], 0) != cudaSuccess)
+            return CG_ERR_CUDA;
+        if (launch_sketch_csr_rows_chunk(rp, ci, v, static_cast<int>(r1 - r0), p->d, static_cast<uint32_t>(p->B),
+                                         static_cast<int>(k0), static_cast<int>(k1), key, p->row_offset + r0, SX,
+                                         status_word(ws), static_cast<int>(p->sketch_ctas), p->scatter_rows,
+                                         st) != cudaSuccess)
+            return CG_ERR_CUDA;
+        if (cudaEventRecord(h->consumed[b], st) != cudaSuccess) return CG_ERR_CUDA;
+    }
+    if ((s = run_contract(p, SX, Yd, ws, L, st)) != CG_OK) return s;
+    return from_cuda(cudaMemcpyAsync(Y, Yd, static_cast<size_t>(p->m) * p->d * sizeof(float), cudaMemcpyDeviceToHost,
+                                     st));
 }
 
 cg_status cg_diag_random_reductions(float *array, int64_t cells, int64_t count, void *stream) {

@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / 32;
-constexpr int kMaxContractItems = 64;  // per instance (bounds the partials buffer)
+constexpr int kMaxContractItems = 256;  // per instance (bounds the partials buffer)
 
 struct BatchInst {
     const int *row_ptr;
@@ -125,11 +125,23 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
         __syncthreads();
         if (s_flag) {  // the last contract item of the instance sums its partials in order
             __threadfence();
+            // Four interleaved running sums (partials g = 0, 4, 8, ... into the first, and so
+            // on), then ((a0 + a1) + a2) + a3: a fixed order with four loads in flight.
             const int md = I.m * I.d;
             for (int o = t; o < md; o += kBThreads) {
-                float acc = 0.0f;
-                for (int g = 0; g < I.n_g; ++g) acc += __ldcg(I.partials + static_cast<size_t>(g) * md + o);
-                I.Y[o] = acc;
+                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+                const float *p = I.partials + o;
+                int g = 0;
+                for (; g + 3 < I.n_g; g += 4) {
+                    a0 += __ldcg(p + static_cast<size_t>(g) * md);
+                    a1 += __ldcg(p + static_cast<size_t>(g + 1) * md);
+                    a2 += __ldcg(p + static_cast<size_t>(g + 2) * md);
+                    a3 += __ldcg(p + static_cast<size_t>(g + 3) * md);
+                }
+                if (g < I.n_g) a0 += __ldcg(p + static_cast<size_t>(g) * md);
+                if (g + 1 < I.n_g) a1 += __ldcg(p + static_cast<size_t>(g + 1) * md);
+                if (g + 2 < I.n_g) a2 += __ldcg(p + static_cast<size_t>(g + 2) * md);
+                I.Y[o] = ((a0 + a1) + a2) + a3;
             }
         }
         __syncthreads();
@@ -165,6 +177,12 @@ struct cg_batch_plan {
 
 namespace {
 
+// Contract items of an instance: at most one per 32-wide slab of B, and kMaxContractItems.
+int64_t max_contract_items(int64_t B) {
+    const int64_t nslabs = (B + kFfmaKT - 1) / kFfmaKT;
+    return std::max<int64_t>(1, std::min<int64_t>(kMaxContractItems, nslabs));
+}
+
 int64_t pow2_floor(int64_t x) {
     int64_t p = 1;
     while (p * 2 <= x) p *= 2;
@@ -189,7 +207,8 @@ void build(cg_batch_plan &P) {
     P.zero_bytes = off - P.counters_off;
     for (int k = 0; k < count; ++k) {
         P.part_off[k] = off;
-        off += align256(static_cast<size_t>(kMaxContractItems) * P.descs[k].m * P.descs[k].d * sizeof(float));
+        off += align256(static_cast<size_t>(max_contract_items(P.descs[k].B)) * P.descs[k].m * P.descs[k].d *
+                        sizeof(float));
     }
     P.insts_off = off;
     off += align256(static_cast<size_t>(count) * sizeof(BatchInst));
@@ -214,7 +233,8 @@ void build(cg_batch_plan &P) {
         const int64_t nslabs = (D.B + kFfmaKT - 1) / kFfmaKT;
         int64_t spg = (P.g_fma + static_cast<int64_t>(D.m) * D.d * kFfmaKT - 1) /
                       (static_cast<int64_t>(D.m) * D.d * kFfmaKT);
-        spg = std::max<int64_t>(spg, (nslabs + kMaxContractItems - 1) / kMaxContractItems);
+        const int64_t cap = max_contract_items(D.B);
+        spg = std::max<int64_t>(spg, (nslabs + cap - 1) / cap);
         spg = std::max<int64_t>(1, std::min(spg, nslabs));
         I.slabs_per_g = static_cast<int>(spg);
         I.n_g = static_cast<int>((nslabs + spg - 1) / spg);
@@ -229,7 +249,15 @@ void build(cg_batch_plan &P) {
             P.items.push_back(BatchItem{k, 0, static_cast<int>(a), static_cast<int>(std::min<int64_t>(a + rows, I.n))});
         }
     }
-    for (int k : order)
+    // Contract items longest first (FMAs per item), so that the short ones fill the end of
+    // the queue and no long item starts last.
+    std::vector<int> gorder(count);
+    for (int k = 0; k < count; ++k) gorder[k] = k;
+    auto item_fma = [&](int k) {
+        return static_cast<int64_t>(P.insts[k].slabs_per_g) * P.insts[k].m * P.insts[k].d;
+    };
+    std::stable_sort(gorder.begin(), gorder.end(), [&](int a, int b) { return item_fma(a) > item_fma(b); });
+    for (int k : gorder)
         for (int g = 0; g < P.insts[k].n_g; ++g) P.items.push_back(BatchItem{k, 1, g, 0});
     // queue capacity for the smallest scatter item (32 rows), so that no tiling choice
     // outgrows the workspace

@@ -24,6 +24,8 @@ struct cg_plan {
     int32_t scatter;        // CG_OPT_SCATTER
     int32_t scatter_passes; // CG_OPT_SCATTER_PASSES (0 = auto)
     int32_t scatter_rows;   // CG_OPT_SCATTER_ROWS (0 = auto)
+    int64_t host_chunk;     // CG_OPT_HOST_CHUNK (0 = auto)
+    void *host_state;       // copy stream and events of cg_apply_csr_host, created on first use
 };
 
 namespace cg {
@@ -67,6 +69,13 @@ cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
                                        cudaStream_t stream);
 int sketch_default_ctas();
+// Rows [0, n) of a chunk of a CSR matrix into SX (no clearing, one pass): row_ptr holds
+// the chunk's n + 1 offsets into the whole matrix, col_idx / vals hold its nonzeros
+// [klo, khi), i.e. nonzero k is col_idx[k - klo]; row i of the chunk is global row
+// row_offset + i.
+cudaError_t launch_sketch_csr_rows_chunk(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                         uint32_t B, int klo, int khi, Key key, int64_t row_offset, float *SX,
+                                         int *status, int ctas, int rows, cudaStream_t stream);
 // Deterministic scatter: exact int64 fixed-point sums (scratch of sketch_fixed_scratch_bytes).
 size_t sketch_fixed_scratch_bytes(int64_t B, int d);
 cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,

@@ -64,15 +64,18 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, int F) {
 // one reduction into SX: fp32, or with FIXED the 64-bit integer to_fixed(x, F) into an
 // integer SX (order-independent sums).  Taller chunks put more nonzeros behind each
 // pair of dependent memory round trips (row_ptr, then the nonzeros), which is what
-// very sparse rows need.  Out-of-range column indices and malformed row offsets are
-// skipped and reported through `bad`.  Only rows whose bucket lies in [blo, bhi) are
-// reduced (bucket-range passes); blo = 0, bhi = B reduces every row.
+// very sparse rows need.  Row offsets index col_idx / vals from klo: nonzero k of the
+// matrix is col_idx[k - klo] (klo = 0 for a whole matrix; the first nonzero of a chunk of
+// rows copied on its own), and offsets outside [klo, nnz] or out of order are malformed.  Out-of-range
+// column indices and malformed row offsets are skipped and reported through `bad`.  Only
+// rows whose bucket lies in [blo, bhi) are reduced (bucket-range passes); blo = 0,
+// bhi = B reduces every row.
 template <bool FIXED, int ROWS>
 __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                               const float *__restrict__ vals, int first, int n, int d, uint32_t B,
-                                              int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
-                                              int *s_rp, uint32_t *s_h, float *s_sg, int &bad, uint32_t blo = 0u,
-                                              uint32_t bhi = 0xFFFFFFFFu) {
+                                              int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
+                                              int F, int *s_rp, uint32_t *s_h, float *s_sg, int &bad,
+                                              uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
     static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128, "chunk height");
     constexpr int R = ROWS / 32;
     const int lane = threadIdx.x & 31;
@@ -98,7 +101,10 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
     if (lane == 0) s_rp[ROWS] = end;
     __syncwarp();
     const int beg = s_rp[0];
-    if (beg < 0 || end > nnz || beg > end) {  // malformed row_ptr: skip the chunk
+    bool ordered = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) ordered &= s_rp[r * 32 + lane] <= s_rp[r * 32 + lane + 1];
+    if (beg < klo || end > nnz || !__all_sync(0xffffffffu, ordered)) {  // malformed row_ptr: skip the chunk
         bad = 1;
         __syncwarp();
         return;
@@ -112,8 +118,8 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
             col[u] = -1;
             v[u] = 0.0f;
             if (k0 + u * 32 < end && k < end) {  // first test warp-uniform: empty slots cost nothing
-                col[u] = ld_stream_i32(col_idx + k, pol);
-                v[u] = ld_stream_f32(vals + k, pol);
+                col[u] = ld_stream_i32(col_idx + (k - klo), pol);
+                v[u] = ld_stream_f32(vals + (k - klo), pol);
             }
         }
 #pragma unroll
@@ -148,13 +154,13 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
 // its bucket lies in [blo, bhi), walks the row's own nonzeros k = row_ptr[i] ..
 // row_ptr[i + 1] - 1, one reduction each.  The warp takes as many steps as its longest
 // row; the lanes' loads of one step fall in the chunk's short, contiguous range of
-// col_idx / vals.  Out-of-range column indices and malformed row offsets are skipped
-// and reported through `bad`.
+// col_idx / vals (indexed from klo as in scatter_chunk).  Out-of-range column indices
+// and malformed row offsets are skipped and reported through `bad`.
 template <bool FIXED>
 __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                                 const float *__restrict__ vals, int first, int n, int d, uint32_t B,
-                                                int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
-                                                int &bad, uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
+                                                int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
+                                                int F, int &bad, uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
     const int lane = threadIdx.x & 31;
     const uint64_t pol = l2_evict_first_policy();
     const int i = first + lane;
@@ -162,7 +168,7 @@ __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr,
     int end = __shfl_down_sync(0xffffffffu, beg, 1);  // row_ptr[i + 1] from the next lane
     if (i < n) {
         if (lane == 31 || i + 1 == n) end = __ldg(row_ptr + i + 1);
-        if (beg < 0 || end > nnz || beg > end) {  // malformed row offsets: skip the row
+        if (beg < klo || end > nnz || beg > end) {  // malformed row offsets: skip the row
             bad = 1;
             end = beg;
         }
@@ -172,8 +178,8 @@ __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr,
         if (h < blo || h >= bhi) end = beg;  // another pass reduces this row
         const size_t base = static_cast<size_t>(h) * d;
         for (int k = beg; k < end; ++k) {
-            const int j = ld_stream_i32(col_idx + k, pol);
-            const float v = ld_stream_f32(vals + k, pol);
+            const int j = ld_stream_i32(col_idx + (k - klo), pol);
+            const float v = ld_stream_f32(vals + (k - klo), pol);
             if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
                 if (FIXED)
                     atomicAdd(static_cast<unsigned long long *>(SX) + base + j, to_fixed(sg * v, F));
@@ -193,8 +199,8 @@ __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr,
                                                 const float *__restrict__ vals, int first, int n, int d, uint32_t B,
                                                 int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
                                                 int *s_rp, uint32_t *s_h, float *s_sg, int &bad) {
-    scatter_chunk<FIXED, 32>(row_ptr, col_idx, vals, first, n, d, B, nnz, key, row_offset, SX, F, s_rp, s_h, s_sg,
-                             bad);
+    scatter_chunk<FIXED, 32>(row_ptr, col_idx, vals, first, n, d, B, nnz, 0, key, row_offset, SX, F, s_rp, s_h,
+                             s_sg, bad);
 }
 
 }  // namespace cg

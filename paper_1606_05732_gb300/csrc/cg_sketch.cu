@@ -25,7 +25,7 @@ constexpr int kUnroll = 4;  // nonzeros in flight per lane
 template <bool FIXED, int ROWS>
 __global__ void __launch_bounds__(kThreads)
 sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
-                  int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *__restrict__ SX,
+                  int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
                   const int *__restrict__ maxbits, int *__restrict__ status, uint32_t blo, uint32_t bhi) {
     constexpr int CH = ROWS == 0 ? 32 : ROWS;
     __shared__ int s_rp[kWarps][ROWS == 0 ? 1 : ROWS + 1];
@@ -37,10 +37,10 @@ sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     int bad = 0;
     for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
         if constexpr (ROWS == 0)
-            scatter_lanes32<FIXED>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, key, row_offset, SX, F, bad, blo,
-                                   bhi);
+            scatter_lanes32<FIXED>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, klo, key, row_offset, SX, F, bad,
+                                   blo, bhi);
         else
-            scatter_chunk<FIXED, ROWS>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, key, row_offset, SX, F,
+            scatter_chunk<FIXED, ROWS>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, klo, key, row_offset, SX, F,
                                        s_rp[w], s_h[w], s_sg[w], bad, blo, bhi);
     }
     if (bad) atomicOr(status, kStatusBounds);
@@ -61,20 +61,21 @@ int chunk_height(int rows) { return rows == 1 ? 32 : rows; }
 
 template <bool FIXED>
 void launch_csr_rows(int rows, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
-                     const float *vals, int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, void *SX,
-                     const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
+                     const float *vals, int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset,
+                     void *SX, const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
     if (rows == 1)
-        sketch_csr_kernel<FIXED, 0><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
-                                                                   row_offset, SX, maxbits, status, blo, bhi);
+        sketch_csr_kernel<FIXED, 0><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                                                   key, row_offset, SX, maxbits, status, blo, bhi);
     else if (rows == 128)
-        sketch_csr_kernel<FIXED, 128><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
-                                                                     row_offset, SX, maxbits, status, blo, bhi);
+        sketch_csr_kernel<FIXED, 128><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz,
+                                                                     klo, key, row_offset, SX, maxbits, status, blo,
+                                                                     bhi);
     else if (rows == 64)
-        sketch_csr_kernel<FIXED, 64><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
-                                                                    row_offset, SX, maxbits, status, blo, bhi);
+        sketch_csr_kernel<FIXED, 64><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                                                    key, row_offset, SX, maxbits, status, blo, bhi);
     else
-        sketch_csr_kernel<FIXED, 32><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
-                                                                    row_offset, SX, maxbits, status, blo, bhi);
+        sketch_csr_kernel<FIXED, 32><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                                                    key, row_offset, SX, maxbits, status, blo, bhi);
 }
 
 // max |x| over the stored values, as the bit pattern of a non-negative float (whose
@@ -201,10 +202,23 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
     for (int p = 0; p < passes; ++p) {
         const uint32_t blo = per * static_cast<uint32_t>(p);
         const uint32_t bhi = p == passes - 1 ? B : blo + per;
-        launch_csr_rows<false>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, nullptr,
-                               status, blo, bhi);
+        launch_csr_rows<false>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, 0, key, row_offset, SX,
+                               nullptr, status, blo, bhi);
     }
     record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_csr_rows_chunk(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                         uint32_t B, int klo, int khi, Key key, int64_t row_offset, float *SX,
+                                         int *status, int ctas, int rows, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    rows = chunk_rows(n, khi - klo, rows);
+    const int nchunks = (n + chunk_height(rows) - 1) / chunk_height(rows);
+    const int need = (nchunks + kWarps - 1) / kWarps;
+    const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
+    launch_csr_rows<false>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, khi, klo, key, row_offset, SX, nullptr,
+                           status, 0u, B);
     return cudaGetLastError();
 }
 
@@ -228,8 +242,8 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
         const int nchunks = (n + chunk_height(rows) - 1) / chunk_height(rows);
         const int need = (nchunks + kWarps - 1) / kWarps;
         const int grid = max(1, min(ctas > 0 ? ctas : sketch_default_ctas(), need));
-        launch_csr_rows<true>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, acc, maxbits,
-                              status, 0u, B);
+        launch_csr_rows<true>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, 0, key, row_offset, acc,
+                              maxbits, status, 0u, B);
     }
     const int64_t blocks = (cells + kThreads - 1) / kThreads;
     fixed_to_float_kernel<<<static_cast<unsigned>(blocks < sms * 8 ? (blocks > 0 ? blocks : 1) : sms * 8), kThreads, 0,
