@@ -106,7 +106,8 @@ typedef enum cg_option {
                                  nonzeros swept 32 at a time), or 1 (one row per lane, each
                                  lane walking its own row) */
     CG_OPT_HOST_CHUNK = 10    /* cg_apply_csr_host: most nonzeros, and most rows, per chunk copied
-                                 to the device; 0 = automatic (2^22), else 32 .. 2^30 */
+                                 to the device; 0 = automatic (nnz / 4 within [2^20, 2^24]), else
+                                 32 .. 2^30 */
 } cg_option;
 
 typedef enum cg_kernel {

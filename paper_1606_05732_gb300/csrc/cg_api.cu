@@ -233,7 +233,10 @@ struct HostCaps {
 
 HostCaps host_caps(const cg_plan &p, int64_t nnz) {
     HostCaps c;
-    const int64_t chunk = p.host_chunk > 0 ? p.host_chunk : (1LL << 22);
+    // automatic: about four chunks (copy of chunk c + 1 hides the scatter of chunk c), each
+    // at least 2^20 and at most 2^24 nonzeros (per-copy overheads vs. pipeline fill)
+    const int64_t chunk =
+        p.host_chunk > 0 ? p.host_chunk : std::max<int64_t>(1LL << 20, std::min<int64_t>(1LL << 24, nnz / 4));
     c.nnz = std::max<int64_t>(1, std::min(nnz, chunk));
     c.rows = std::max<int64_t>(1, std::min(p.n, chunk));
     c.rp_off = 0;
