@@ -94,9 +94,13 @@ typedef enum cg_option {
     CG_OPT_SKETCH_CTAS = 5,   /* CTAs of the scatter kernel; 0 = automatic */
     CG_OPT_TIMING = 6,        /* 1: record CUDA events around each main kernel launch
                                  (read with cg_plan_timing); 0 (default): off */
-    CG_OPT_SCATTER = 7,       /* CSR scatter algorithm (atomic mode): 0 = automatic (default),
-                                 1 = one L2 reduction per nonzero, 2 = partition the nonzeros by
-                                 bucket range and accumulate each range in shared memory */
+    CG_OPT_SCATTER = 7,       /* CSR scatter algorithm (atomic mode): 0 = automatic (default: 3
+                                 when SX is larger than 60 % of the L2, else 1), 1 = one L2
+                                 reduction per nonzero, 2 = partition the nonzeros by bucket
+                                 range and accumulate each range in shared memory, 3 = reduce
+                                 the rows of buckets below B/2 at once and write the others as
+                                 records reduced by a second pass (each half of SX in L2 in
+                                 turn; workspace + 8 bytes per nonzero; needs B d < 2^32) */
     CG_OPT_SCATTER_PASSES = 8, /* bucket-range passes of the atomic CSR scatter (each pass streams
                                  the CSR and reduces the rows of one range of buckets, keeping
                                  that range of SX in L2); 0 = automatic (one pass), 1..16 forced */

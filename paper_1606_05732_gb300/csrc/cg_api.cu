@@ -139,6 +139,20 @@ int num_sms() {
     return sms;
 }
 
+int l2_bytes() {
+    static int cache[kMaxDevices] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cache[dev] == 0 && cudaDeviceGetAttribute(&cache[dev], cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        cache[dev] = 0;
+    }
+    return cache[dev];
+}
+
 int resident_ctas_per_sm(const void *kernel, int threads, size_t dyn_smem, int tmem_cols) {
     int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0, blocks_sm = 0;
     cudaFuncAttributes fa;
@@ -204,6 +218,18 @@ bool use_partition(const cg_plan &p) {
     return p.scatter == 2 && partition_supported(p);
 }
 
+// Whether a CSR scatter through plan p defers half of SX to a second pass: on request
+// (CG_OPT_SCATTER = 3), or automatically when SX is larger than 60 % of the L2, where
+// random reductions into it start to miss (and bucket-range passes are not forced).
+bool use_deferred(const cg_plan &p) {
+    if (p.deterministic || use_partition(p) || !deferred_supported(p.B, p.d)) return false;
+    if (p.scatter == 3) return true;
+    if (p.scatter != 0 || p.scatter_passes > 0) return false;
+    const double sx = static_cast<double>(p.B) * p.d * sizeof(float);
+    const int l2 = l2_bytes();
+    return l2 > 0 && sx > 0.6 * l2;
+}
+
 // Scratch bytes of the CSR scatter through plan p (region C).
 size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
     if (p.deterministic) return sketch_fixed_scratch_bytes(p.B, p.d);
@@ -211,6 +237,7 @@ size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
         *part = partition_layout(p, nnz);
         return part->bytes;
     }
+    if (use_deferred(p)) return sketch_deferred_scratch_bytes(nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas)));
     return 0;
 }
 
@@ -328,6 +355,12 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
                                                  p->row_offset, SX, region(ws, L.c_off), status_word(ws),
                                                  static_cast<int>(p->sketch_ctas), p->scatter_rows,
                                                  timing_pair(p, CG_KERNEL_SKETCH), st));
+    if (use_deferred(*p))
+        return from_cuda(launch_sketch_csr_deferred(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
+                                                    static_cast<uint32_t>(p->B), static_cast<int>(nnz),
+                                                    make_key(p->seed), p->row_offset, SX, status_word(ws),
+                                                    region(ws, L.c_off), static_cast<int>(p->sketch_ctas),
+                                                    p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st));
     if (use_partition(*p))
         return from_cuda(launch_sketch_csr_partitioned(
             row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), static_cast<int>(nnz),
@@ -490,7 +523,7 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             p->timing = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_SCATTER:
-            if (value < 0 || value > 2) return CG_ERR_INVALID_ARG;
+            if (value < 0 || value > 3) return CG_ERR_INVALID_ARG;
             p->scatter = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_SCATTER_PASSES:

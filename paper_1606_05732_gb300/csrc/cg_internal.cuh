@@ -82,6 +82,19 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, void *scratch,
                                     int *status, int ctas, int rows, const EventPair *ev, cudaStream_t stream);
 
+// ---- deferred scatter (cg_sketch_defer.cu) -----------------------------------------
+// SX split at bucket B/2: one CSR pass reduces the lower half and writes the rest as
+// records, a second pass reduces the records (for an SX larger than the L2 holds).
+bool deferred_supported(int64_t B, int d);
+int sketch_deferred_ctas(int ctas);
+size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas);
+cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                       uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream);
+
+// Bytes of the L2 of the current device (cached per device; 0 without a device).
+int l2_bytes();
+
 // ---- partitioned scatter (cg_sketch_part.cu) --------------------------------------
 struct PartLayout {
     int SB = 0;           // buckets per slice

@@ -1,0 +1,262 @@
+// cg_sketch_defer.cu -- SX = S.X (Section 1.1, the O(nnz(X)) stage) for an SX too large
+// for the L2 to hold, in one pass over the CSR plus one pass over records.
+//
+// One fp32 reduction per nonzero runs at the L2's atomic rate only while the reduced
+// array stays in L2; past that (on GB300 from about 100 MB on) most reductions miss and
+// the rate falls several-fold.  So SX is split at bucket bsplit = B/2:
+//   pass 1  streams the CSR once, hashes every row once, reduces the nonzeros of rows
+//           with h < bsplit into SX at once, and writes those of the other rows as
+//           8-byte records (h d + j, sigma x) into its CTA's region of a records buffer
+//           (regions follow the nonzero order: CTA c owns rows [c R, (c+1) R) and the
+//           record slots of their nonzeros; one shared atomic per warp and 32 nonzeros
+//           hands out slots, so records are written compactly and coalesced);
+//   pass 2  streams each region's records and reduces them into the upper part of SX,
+//           which is then the one in L2.
+// Each half of SX is half the size, and the extra traffic is the records, 16 bytes per
+// deferred nonzero (written once, read once, with an evict-first L2 policy).  Sums are
+// fp32 in an order that depends on timing, as with the atomic scatter.
+#include "cg_internal.cuh"
+#include "cg_scatter.cuh"
+
+namespace cg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ void st_stream_u2(uint2 *p, uint2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Rows [first, min(first + ROWS, n)) staged as in scatter_chunk: lane l loads the
+// row_ptr entries of rows first + l + 32 r and hashes those rows into s_rp[ROWS + 1],
+// s_h[ROWS], s_sg[ROWS].  Returns the chunk's nonzero range [beg, end), or false
+// (setting `bad`) if the offsets leave [0, nnz] or are out of order.  All lanes of
+// the warp take part.
+template <int ROWS>
+__device__ __forceinline__ bool stage_chunk(const int *__restrict__ row_ptr, int first, int n, int nnz, uint32_t B,
+                                            Key key, int64_t row_offset, int *s_rp, uint32_t *s_h, float *s_sg,
+                                            uint64_t pol, int &beg, int &end, int &bad) {
+    static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128, "chunk height");
+    constexpr int R = ROWS / 32;
+    const int lane = threadIdx.x & 31;
+    const int last = min(first + ROWS, n);
+    end = __ldg(row_ptr + last);
+    int rp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {  // all row_ptr loads in flight before the hashing
+        const int i = first + r * 32 + lane;
+        rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = first + r * 32 + lane;
+        uint32_t h = 0;
+        float sg = 0.0f;
+        if (i < n) hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+        s_rp[r * 32 + lane] = rp[r];
+        s_h[r * 32 + lane] = h;
+        s_sg[r * 32 + lane] = sg;
+    }
+    if (lane == 0) s_rp[ROWS] = end;
+    __syncwarp();
+    beg = s_rp[0];
+    bool ordered = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) ordered &= s_rp[r * 32 + lane] <= s_rp[r * 32 + lane + 1];
+    if (beg < 0 || end > nnz || !__all_sync(0xffffffffu, ordered)) {  // malformed row_ptr: skip the chunk
+        bad = 1;
+        __syncwarp();
+        return false;
+    }
+    return true;
+}
+
+// Pass 1 on one staged chunk: nonzeros of rows with h < bsplit are reduced into SX;
+// the others become records appended to records[rec_lo, rec_hi) through *s_count.
+// The nonzeros are swept 32 x kScatterUnroll at a time with coalesced evict-first
+// loads, each finding its row by a log2(ROWS)-step binary search over s_rp.  Bad
+// column indices, and records that would leave the region (only possible with
+// malformed offsets), are dropped and reported through `bad`.
+template <int ROWS>
+__device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, const float *__restrict__ vals, int beg,
+                                            int end, int d, float *__restrict__ SX, uint32_t bsplit,
+                                            uint2 *__restrict__ records, int rec_lo, int rec_hi, int *s_count,
+                                            const int *s_rp, const uint32_t *s_h, const float *s_sg, uint64_t pol,
+                                            int &bad) {
+    const int lane = threadIdx.x & 31;
+    for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
+        int col[kScatterUnroll];
+        float v[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const int k = k0 + u * 32 + lane;
+            col[u] = -1;
+            v[u] = 0.0f;
+            if (k0 + u * 32 < end && k < end) {  // first test warp-uniform: empty slots cost nothing
+                col[u] = ld_stream_i32(col_idx + k, pol);
+                v[u] = ld_stream_f32(vals + k, pol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            if (k0 + u * 32 >= end) break;  // warp-uniform
+            const int k = k0 + u * 32 + lane;
+            bool defer = false;
+            uint32_t cell = 0;
+            float x = 0.0f;
+            if (k < end) {
+                int lo = 0;
+#pragma unroll
+                for (int step = ROWS / 2; step > 0; step >>= 1)
+                    if (s_rp[lo + step] <= k) lo += step;
+                const int j = col[u];
+                const uint32_t hb = s_h[lo];
+                if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
+                    cell = hb * static_cast<uint32_t>(d) + static_cast<uint32_t>(j);
+                    x = s_sg[lo] * v[u];
+                    if (hb < bsplit)
+                        atomicAdd(SX + cell, x);
+                    else
+                        defer = true;
+                } else {
+                    bad = 1;
+                }
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, defer);
+            if (mask == 0u) continue;  // warp-uniform
+            int base = 0;
+            if (lane == 0) base = atomicAdd(s_count, __popc(mask));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (defer) {
+                const int at = rec_lo + base + __popc(mask & ((1u << lane) - 1u));
+                if (at < rec_hi)
+                    st_stream_u2(records + at, make_uint2(cell, __float_as_uint(x)), pol);
+                else
+                    bad = 1;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Pass 1: CTA c takes rows [c R, min((c+1) R, n)) (R a multiple of ROWS) and the
+// record slots row_ptr[c R] .. row_ptr[min((c+1) R, n)] - 1; it writes how many records
+// it made to counts[c] (0 for a CTA whose region offsets are malformed).
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
+                  int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, float *__restrict__ SX,
+                  uint32_t bsplit, int rows_per_cta, uint2 *__restrict__ records, int *__restrict__ counts,
+                  int *__restrict__ status) {
+    __shared__ int s_rp[kWarps][ROWS + 1];
+    __shared__ uint32_t s_h[kWarps][ROWS];
+    __shared__ float s_sg[kWarps][ROWS];
+    __shared__ int s_count;
+    const int w = threadIdx.x >> 5;
+    const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
+    const int r1 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(r0) + rows_per_cta));
+    const int rec_lo = __ldg(row_ptr + r0);
+    const int rec_hi = __ldg(row_ptr + r1);
+    if (rec_lo < 0 || rec_hi > nnz || rec_lo > rec_hi) {  // uniform over the CTA
+        if (threadIdx.x == 0) {
+            counts[blockIdx.x] = 0;
+            atomicOr(status, kStatusBounds);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const uint64_t pol = l2_evict_first_policy();
+    int bad = 0;
+    for (int first = r0 + w * ROWS; first < r1; first += kWarps * ROWS) {
+        int beg, end;
+        if (stage_chunk<ROWS>(row_ptr, first, r1, nnz, B, key, row_offset, s_rp[w], s_h[w], s_sg[w], pol, beg, end,
+                              bad))
+            split_chunk<ROWS>(col_idx, vals, beg, end, d, SX, bsplit, records, rec_lo, rec_hi, &s_count, s_rp[w],
+                              s_h[w], s_sg[w], pol, bad);
+    }
+    if (bad) atomicOr(status, kStatusBounds);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
+}
+
+// Pass 2: CTA c reduces the counts[c] records of its region into SX.
+__global__ void __launch_bounds__(kThreads)
+replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, const uint2 *__restrict__ records,
+                      const int *__restrict__ counts, uint32_t cells, float *__restrict__ SX) {
+    const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
+    const int r1 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(r0) + rows_per_cta));
+    const int start = __ldg(row_ptr + r0);
+    // records were written only inside [row_ptr[r0], row_ptr[r1]) (pass 1 set counts to 0
+    // where these offsets were malformed)
+    const int cnt = min(counts[blockIdx.x], __ldg(row_ptr + r1) - start);
+    if (cnt <= 0) return;
+    const uint64_t pol = l2_evict_first_policy();
+    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        const uint2 r = ld_stream_u2(records + start + i, pol);
+        if (r.x < cells) atomicAdd(SX + r.x, __uint_as_float(r.y));
+    }
+}
+
+int staged_rows(int n, int nnz, int forced) {
+    if (forced == 32 || forced == 64 || forced == 128) return forced;
+    const double per_row = n > 0 ? static_cast<double>(nnz) / n : 0.0;
+    if (per_row * 32 >= 96.0) return 32;
+    if (per_row * 64 >= 96.0) return 64;
+    return 128;
+}
+
+}  // namespace
+
+bool deferred_supported(int64_t B, int d) { return static_cast<uint64_t>(B) * static_cast<uint64_t>(d) < (1ull << 32); }
+
+size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas) {
+    return align256(static_cast<size_t>(nnz) * sizeof(uint2)) + align256(static_cast<size_t>(ctas) * sizeof(int));
+}
+
+int sketch_deferred_ctas(int ctas) { return ctas > 0 ? ctas : sketch_default_ctas(); }
+
+cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                       uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
+    if (e != cudaSuccess || n == 0) return e;
+    const int G = sketch_deferred_ctas(ctas);
+    const int H = staged_rows(n, nnz, rows);
+    const int per = (n + G - 1) / G;
+    const int rows_per_cta = (per + H - 1) / H * H;
+    const int used = (n + rows_per_cta - 1) / rows_per_cta;
+    uint2 *records = static_cast<uint2 *>(scratch);
+    int *counts = reinterpret_cast<int *>(static_cast<char *>(scratch) + align256(static_cast<size_t>(nnz) * sizeof(uint2)));
+    const uint32_t bsplit = B / 2;
+    record(ev, true, stream);
+    switch (H) {
+        case 128:
+            split_pass_kernel<128><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                                  SX, bsplit, rows_per_cta, records, counts, status);
+            break;
+        case 64:
+            split_pass_kernel<64><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                                 SX, bsplit, rows_per_cta, records, counts, status);
+            break;
+        default:
+            split_pass_kernel<32><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                                 SX, bsplit, rows_per_cta, records, counts, status);
+            break;
+    }
+    replay_records_kernel<<<used, kThreads, 0, stream>>>(row_ptr, n, rows_per_cta, records, counts,
+                                                         B * static_cast<uint32_t>(d), SX);
+    record(ev, false, stream);
+    return cudaGetLastError();
+}
+
+}  // namespace cg

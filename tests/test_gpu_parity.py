@@ -57,6 +57,22 @@ def test_hash_sign_bit_exact(B):
         np.testing.assert_array_equal(s.cpu().numpy(), ws)
 
 
+def test_gaussian_entries_many():
+    """8.4 M entries (2^21 Philox calls, so 2^22 uniforms of each role: radius and
+    angle) against the FP64 Box-Muller of the same words.  Per entry the fp32 result
+    carries a few ulp of relative error in the radius sqrt(-2 ln u) and a few 1e-8 of
+    absolute error in cos / sin of 2 pi u, so |z - z64| <= 1e-6 (1 + |z64|); over all
+    entries the relative Frobenius error is below 2e-7."""
+    R, C = 8, 1 << 20
+    got = cg().generate_gaussian(77, 1, R, 0, R, 0, C).cpu().numpy().astype(np.float64)
+    want = oracle.gaussian_block(77, 1, R, 0, R, 0, C)
+    err = np.abs(got - want)
+    print(f"max |dz| = {err.max():.3e}, max |dz|/(1+|z|) = {(err / (1 + np.abs(want))).max():.3e}, "
+          f"rel Frobenius {rel(got, want):.3e}")
+    assert (err <= 1e-6 * (1.0 + np.abs(want))).all()
+    assert rel(got, want) < 2e-7
+
+
 @pytest.mark.parametrize("tag,R", [(1, 8), (1, 13), (2, 128), (1, 1)])
 def test_gaussian_entries(tag, R):
     got = cg().generate_gaussian(5, tag, R, 0, R, 1000, 1700).cpu().numpy()
@@ -92,7 +108,7 @@ def make_input(n, d, seed, kind):
     return synth.csr_bernoulli(n, d, p, seed=seed, values="uniform" if kind.endswith("u") else "normal")
 
 
-@pytest.mark.parametrize("scatter", ["atomic", "partition"])
+@pytest.mark.parametrize("scatter", ["atomic", "partition", "deferred"])
 @pytest.mark.parametrize("n,d,m,B,seed,kind", CASES)
 def test_apply_csr_parity(n, d, m, B, seed, kind, scatter):
     X = make_input(n, d, seed, kind)
@@ -154,6 +170,36 @@ def test_scatter_chunk_rows_and_passes(n, d, m, B, seed, kind, rows, passes):
     SXd = det.sketch_csr(rp, ci, v).cpu().numpy()
     det.check()
     assert rel(SXd, SXo) < 1e-6
+
+
+@pytest.mark.parametrize("rows", [32, 64, 128])
+def test_deferred_scatter_edges(rows):
+    """The deferred scatter (rows of the upper half of the buckets written as records,
+    reduced by a second pass): CTA row ranges with ragged ends and empty rows, a row
+    offset (shard), and the error report for a bad column index and for out-of-order
+    offsets, which it skips like the one-pass scatter."""
+    from paper_1606_05732_gb300 import _lib
+    n, d, m, B, seed = 70001, 37, 13, 3001, 21
+    X = synth.csr_ragged(n, d, seed=5, max_row=6)
+    rp, ci, v = dev_csr(X)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="deferred", scatter_rows=rows, row_offset=12345)
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=12345, return_sx=True)
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL
+    bad_ci = ci.clone()
+    bad_ci[X.nnz // 2] = d + 3
+    plan.sketch_csr(rp, bad_ci, v)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    bad_rp = rp.clone()
+    bad_rp[n // 2], bad_rp[n // 2 + 1] = rp[n // 2 + 1].item() + 1, rp[n // 2].item()
+    plan.sketch_csr(bad_rp, ci, v)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    plan.check()
 
 
 def test_partition_overflow_path():
