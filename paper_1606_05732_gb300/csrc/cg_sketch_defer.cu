@@ -201,7 +201,17 @@ replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, 
     const int cnt = min(counts[blockIdx.x], __ldg(row_ptr + r1) - start);
     if (cnt <= 0) return;
     const uint64_t pol = l2_evict_first_policy();
-    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+    constexpr int kInFlight = 4;  // record loads in flight per thread before their reductions
+    int i = threadIdx.x;
+    for (; i + (kInFlight - 1) * kThreads < cnt; i += kInFlight * kThreads) {
+        uint2 r[kInFlight];
+#pragma unroll
+        for (int u = 0; u < kInFlight; ++u) r[u] = ld_stream_u2(records + start + i + u * kThreads, pol);
+#pragma unroll
+        for (int u = 0; u < kInFlight; ++u)
+            if (r[u].x < cells) atomicAdd(SX + r[u].x, __uint_as_float(r[u].y));
+    }
+    for (; i < cnt; i += kThreads) {
         const uint2 r = ld_stream_u2(records + start + i, pol);
         if (r.x < cells) atomicAdd(SX + r.x, __uint_as_float(r.y));
     }
