@@ -413,10 +413,18 @@ def run_ours(args):
     rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
     plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter, precision=args.precision,
                                  scatter_passes=args.scatter_passes, scatter_rows=args.scatter_rows)
-    partitioned = args.scatter == "partition"  # auto: the atomic scatter
-    scatter_kernel = ("partition_kernel+accumulate_kernel" if partitioned else "sketch_csr_kernel")
-    scatter_src = (("cg_sketch_part.cu", "cg_rng.cuh") if partitioned
-                   else ("cg_sketch.cu", "cg_scatter.cuh", "cg_rng.cuh"))
+    partitioned = args.scatter == "partition"
+    # automatic: the deferred two-pass scatter once SX exceeds 60 % of the L2, else one pass
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    deferred = args.scatter == "deferred" or (args.scatter == "auto" and args.scatter_passes == 0
+                                              and 4 * B * d > 0.6 * l2 and B * d < (1 << 32))
+    if partitioned:
+        scatter_kernel, scatter_src = "partition_kernel+accumulate_kernel", ("cg_sketch_part.cu", "cg_rng.cuh")
+    elif deferred:
+        scatter_kernel = "split_pass_kernel+replay_records_kernel"
+        scatter_src = ("cg_sketch_defer.cu", "cg_scatter.cuh", "cg_rng.cuh")
+    else:
+        scatter_kernel, scatter_src = "sketch_csr_kernel", ("cg_sketch.cu", "cg_scatter.cuh", "cg_rng.cuh")
     Y = torch.empty(m, d, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -462,7 +470,7 @@ def run_ours(args):
     sketch_avg_s = (sketch_ms / max(1, sketch_n)) / 1e3
     achieved = alg_bytes / sketch_avg_s / 1e9
     src = source_hash(*scatter_src)
-    traffic = NCU_TRAFFIC.get((src, args.workload)) if not partitioned else None
+    traffic = NCU_TRAFFIC.get((src, args.workload))
     red_ceiling = reduction_ceiling(dev, nnz, B * d) if rank == 0 else None
 
     # plain G~.X on the same input
