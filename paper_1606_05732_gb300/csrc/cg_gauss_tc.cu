@@ -61,8 +61,14 @@ struct Cfg {
     static constexpr uint32_t kTmemCols = NT < 32 ? 32 : NT;
 };
 
+// Threads of the bf16 kernel: 512 for the split form with N tiles of 128 or more (its two
+// operand sets leave room for one CTA per SM, so the Gaussians are drawn by 16 warps),
+// else 256 (several CTAs per SM).
 template <int NT, bool SPLIT3>
-__global__ void __launch_bounds__(kThreads, 1)
+constexpr int bf16_threads() { return SPLIT3 && NT >= 128 ? 512 : 256; }
+
+template <int NT, bool SPLIT3>
+__global__ void __launch_bounds__(bf16_threads<NT, SPLIT3>(), 1)
 contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_cta,
                         float *__restrict__ part, int *__restrict__ status) {
     using C = Cfg<NT, SPLIT3>;
@@ -118,7 +124,7 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
         uint8_t *b_lo = a_lo + C::kA;
 
         // A = G[m0 .. m0+128, k0 .. k0+64): blocks of 4 rows (one Philox call) x 4 columns.
-        for (int q = t; q < (kM / 4) * (kBK / 4); q += kThreads) {
+        for (int q = t; q < (kM / 4) * (kBK / 4); q += bf16_threads<NT, SPLIT3>()) {
             const int gl = q >> 4;
             const int kq = q & 15;
             const uint64_t g = static_cast<uint64_t>((m0 >> 2) + gl);
@@ -148,7 +154,7 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
             }
         }
         // B^T = SX[k0 .. k0+64, n0 .. n0+NT) stored [n][k].
-        for (int q = t; q < NT * (kBK / 4); q += kThreads) {
+        for (int q = t; q < NT * (kBK / 4); q += bf16_threads<NT, SPLIT3>()) {
             const int nl = q % NT;
             const int kq = q / NT;
             float h[4], l[4];
@@ -200,13 +206,17 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
     tc::fence_after_sync();
     __syncthreads();
 
-    // Epilogue: warps w and w+4 share TMEM lanes 32(w%4) .. +32 and split the columns.
+    // Epilogue: warps w, w+4, w+8, ... share TMEM lanes 32(w%4) .. +32 and split the
+    // columns (at least 32 each: bf16_threads gives 512 threads only for NT >= 128).
+    constexpr int kGroups = bf16_threads<NT, SPLIT3>() / 128;
+    constexpr int kCols = NT / kGroups;
+    static_assert(kCols % 32 == 0, "epilogue column split");
     const int quad = warp & 3;
-    const int half = warp >> 2;
+    const int grp = warp >> 2;
     const int row = quad * 32 + lane;
     const int grow = m0 + row;
     float *out = part + static_cast<size_t>(blockIdx.x) * m * d;
-    for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 32) {
+    for (int c0 = grp * kCols; c0 < (grp + 1) * kCols; c0 += 32) {
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0), r);
         tc::tmem_ld_wait();
@@ -237,7 +247,8 @@ cudaError_t launch_tc(const float *SX, int m, int d, int64_t B, Key key, int nsp
     if (e != cudaSuccess) return e;
     dim3 grid(used, (d + NT - 1) / NT, (m + kM - 1) / kM);
     record(ev, true, stream);
-    contract_tc_bf16_kernel<NT, SPLIT3><<<grid, kThreads, smem, stream>>>(SX, m, d, B, key, per, partials, status);
+    contract_tc_bf16_kernel<NT, SPLIT3><<<grid, bf16_threads<NT, SPLIT3>(), smem, stream>>>(SX, m, d, B, key, per,
+                                                                                      partials, status);
     record(ev, false, stream);
     return cudaGetLastError();
 }
@@ -507,7 +518,8 @@ int ctas_bf16() {
     using C = Cfg<NT, SPLIT3>;
     static int n = 0;
     if (n == 0)
-        n = resident_ctas_per_sm(reinterpret_cast<const void *>(contract_tc_bf16_kernel<NT, SPLIT3>), kThreads,
+        n = resident_ctas_per_sm(reinterpret_cast<const void *>(contract_tc_bf16_kernel<NT, SPLIT3>),
+                                 bf16_threads<NT, SPLIT3>(),
                                  C::kSmem, static_cast<int>(C::kTmemCols));
     return n;
 }
