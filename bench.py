@@ -568,7 +568,9 @@ def run_ours(args):
                       "speedup_countgauss_over_plain": plain_ms / ms_step},
             "e2e": {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "cg_apply_csr_host"},
-            "gpu_launches": 3 * args.steps,
+            # per step: the scatter (two kernels when deferred, three when partitioned), the
+            # contraction and its split-K sum
+            "gpu_launches": (4 if deferred else (5 if partitioned else 3)) * args.steps,
             "clocks": clk.summary(),
             "deterministic": {"ms_per_step": det_ms, "value": world * nnz / (det_ms / 1e3), "unit": UNIT},
             "rows": rows,
