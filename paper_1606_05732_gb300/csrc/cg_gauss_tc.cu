@@ -52,6 +52,20 @@ __device__ __forceinline__ void split_bf16(float x, float &hi, float &lo) {
     lo = x - hi;
 }
 
+// L2 prefetch of rows [r0, r0 + rows) of the row-major B x d fp32 SX (clipped to B):
+// one contiguous range, trimmed to whole 16-byte units and to 1 MB; skipped if SX is not
+// 16-byte aligned.
+__device__ __forceinline__ void prefetch_rows(const float *SX, int64_t r0, int rows, int64_t B, int d) {
+    if (r0 >= B || (reinterpret_cast<uintptr_t>(SX) & 15) != 0) return;
+    const int64_t r1 = r0 + rows < B ? r0 + rows : B;
+    const uint64_t first = static_cast<uint64_t>(r0) * d * sizeof(float);
+    const uint64_t last = static_cast<uint64_t>(r1) * d * sizeof(float);
+    const uint64_t a = (first + 15) & ~15ull;
+    uint64_t b = last & ~15ull;
+    if (b > a + (1ull << 20)) b = a + (1ull << 20);  // at most 1 MB per hint
+    if (b > a) tc::prefetch_l2_bulk(reinterpret_cast<const char *>(SX) + a, static_cast<uint32_t>(b - a));
+}
+
 template <int NT, bool SPLIT3>
 struct Cfg {
     static constexpr uint32_t kA = kM * kBK * 2;  // 16 KB
@@ -113,6 +127,8 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
     for (int it = 0; it < nmine; ++it) {
         const int s = it & 1;
         const int64_t k0 = (s_begin + it) * kBK;
+        // the SX rows of the next slab into L2 while this slab's G tile is drawn
+        if (t == 0 && it + 1 < nmine) prefetch_rows(SX, k0 + kBK, kBK, B, d);
         if (it >= 2 && !wait_stage(tc::smem_u32(&mbar[s]), static_cast<uint32_t>(((it >> 1) - 1) & 1))) {
             atomicOr(status, kStatusTimeout);
             abort_flag = 1;
@@ -369,6 +385,8 @@ contract_tc_fp8_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Ke
     for (int it = 0; it < nmine; ++it) {
         const int s = it & 1;
         const int64_t k0 = (s_begin + it) * kBK8;
+        // the SX rows of the next slab into L2 while this slab's G tile is drawn
+        if (t == 0 && it + 1 < nmine) prefetch_rows(SX, k0 + kBK8, kBK8, B, d);
         uint8_t *stage = gbase + s * C::kStage;
         uint8_t *a_hi = stage;
         uint8_t *b_hi = stage + C::kA;
