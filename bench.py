@@ -311,15 +311,28 @@ def _grad_row(dev, reps, csr_dev, stream):
     Xd = torch.from_numpy(synth.dense_normal(w["n"], w["d"], seed=w["seed"])).to(dev)
     Xs = synth.csr_bernoulli(w["n"], w["d"], w["p"], seed=w["seed"])
     rp, ci, v = csr_dev(Xs)
+    from paper_1606_05732_gb300 import _lib
     plan = countgauss.CountGauss(w["n"], w["d"], w["m"], w["B"], w["seed"])
     dY = torch.randn(w["m"], w["d"], device=dev)
+    plan.apply_dense(Xd)
+    plan.adjoint(dY)
+    plan.enable_timing(True)
+    for k in (_lib.KERNEL_SKETCH, _lib.KERNEL_GATHER):
+        plan.kernel_time(k)
     fwd = _time_calls(lambda: plan.apply_dense(Xd), reps, stream)
+    sk_ms, sk_n = plan.kernel_time(_lib.KERNEL_SKETCH)
     bwd = _time_calls(lambda: plan.adjoint(dY), reps, stream)
+    ga_ms, ga_n = plan.kernel_time(_lib.KERNEL_GATHER)
+    plan.enable_timing(False)
     bwd_s = _time_calls(lambda: plan.adjoint(dY, rp, ci), reps, stream)
     dense_bytes = 4 * w["n"] * w["d"]
-    rows["grad_n1M_d64"] = {"apply_dense_ms": fwd, "apply_dense_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / fwd / 1e6,
-                            "adjoint_dense_ms": bwd, "adjoint_dense_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / bwd / 1e6,
-                            "adjoint_csr_ms": bwd_s, "adjoint_csr_nnz": Xs.nnz}
+    sk = sk_ms / max(1, sk_n)
+    ga = ga_ms / max(1, ga_n)
+    rows["grad_n1M_d64"] = {"apply_dense_ms": fwd, "adjoint_dense_ms": bwd, "adjoint_csr_ms": bwd_s,
+                            "adjoint_csr_nnz": Xs.nnz,
+                            # the dense scatter and the dense gather kernels alone (CUDA events)
+                            "dense_scatter_kernel_ms": sk, "dense_scatter_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / sk / 1e6,
+                            "dense_gather_kernel_ms": ga, "dense_gather_gbs": (dense_bytes + 4 * w["B"] * w["d"]) / ga / 1e6}
     del Xd, rp, ci, v
     return rows
 
