@@ -10,8 +10,9 @@
 // contract item every scatter item has already been claimed by a running CTA that never
 // waits: the wait on instance k's scatter counter always ends.  It is bounded anyway
 // (about two seconds of SM clock by default); on expiry the item sets the timeout bit
-// of the status word and contributes zeros.  The contract item that completes instance
-// k's count sums the partials in a fixed order into Y_k.
+// of the status word and contributes zeros.  The partials are summed in a fixed order in
+// two levels: the item that completes a group of 32 items adds their partials, the one
+// that completes the last group adds the group sums into Y_k.
 //
 // The plan sizes the items (target nonzeros per scatter item, target FMAs per contract
 // item, CTAs per SM); cg_batch_autotune times a small grid of these choices on the
@@ -32,19 +33,25 @@ namespace {
 
 constexpr int kBThreads = 256;
 constexpr int kBWarps = kBThreads / 32;
-constexpr int kMaxContractItems = 256;  // per instance (bounds the partials buffer)
+constexpr int kMaxContractItems = 1024;  // per instance (bounds the partials buffer)
+constexpr int kSumGroup = 32;            // partials summed per group in the two-level sum
+constexpr int kMaxGroups = kMaxContractItems / kSumGroup;
+constexpr int kMaxRowsPerItem = 16384;  // per scatter item
+constexpr int kNormalCost = 48;         // FMA-equivalents per Gaussian drawn (item sizing)
 
 struct BatchInst {
     const int *row_ptr;
     const int *col_idx;
     const float *vals;
     float *SX;
-    float *partials;
+    float *partials;  // [part_cap] item partials, then [kMaxGroups] group sums, each m x d
     float *Y;
     int n, d, m, nnz;
     uint32_t B;
     Key key;
     int n_s, n_g;     // scatter / contract items of this instance
+    int part_cap;     // item partial slots before the group sums
+    int lanes;        // 1: scatter one row per lane (instances with under one nonzero per row)
     int slabs_per_g;  // 32-wide K slabs per contract item
     int rows_per_s;   // rows per scatter item
 };
@@ -55,15 +62,49 @@ struct BatchItem {
     int a, b;
 };
 
+// out[o] = slots[g0][o] + slots[g0 + 1][o] + ... + slots[g1 - 1][o] in that order, for
+// o < md (slots are md floats apart); each thread keeps kSumOut outputs (stride
+// kBThreads), so kSumOut loads are in flight.  Called by all threads of the CTA.
+__device__ __forceinline__ void sum_slots(const float *slots, int g0, int g1, int md, float *out) {
+    constexpr int kSumOut = 16;
+    const int t = threadIdx.x;
+    for (int base = t; base < md; base += kBThreads * kSumOut) {
+        float acc[kSumOut];
+#pragma unroll
+        for (int k = 0; k < kSumOut; ++k) acc[k] = 0.0f;
+        for (int g = g0; g < g1; ++g) {
+            const float *p = slots + static_cast<size_t>(g) * md + base;
+#pragma unroll
+            for (int k = 0; k < kSumOut; ++k)
+                if (base + k * kBThreads < md) acc[k] += __ldcg(p + k * kBThreads);
+        }
+#pragma unroll
+        for (int k = 0; k < kSumOut; ++k)
+            if (base + k * kBThreads < md) out[base + k * kBThreads] = acc[k];
+    }
+}
+
+// Hint: bring [p, p + bytes) into L2, trimmed inward to whole 16-byte units (so it never
+// reaches outside the range); nothing waits on it.
+__device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes) {
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~static_cast<uintptr_t>(15);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes) & ~static_cast<uintptr_t>(15);
+    for (uintptr_t q = a; q < e; q += (1u << 20)) {  // at most 1 MB per hint
+        const uint32_t len = static_cast<uint32_t>(e - q < (1u << 20) ? e - q : (1u << 20));
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(len) : "memory");
+    }
+}
+
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__global__ void __launch_bounds__(kBThreads)
+__global__ void __launch_bounds__(kBThreads, 4)  // four CTAs per SM fit (at most 64 registers)
 batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ items, int n_items,
-             int *__restrict__ head, int *__restrict__ s_done, int *__restrict__ g_done, long long wait_cycles,
+             int *__restrict__ head, int *__restrict__ s_done, int *__restrict__ g_done, int *__restrict__ grp_done,
+             long long wait_cycles,
              int *__restrict__ status) {
     __shared__ __align__(16) float raw[FfmaShape<4>::kRawFloats];
     __shared__ int s_rp[kBWarps][33];
@@ -82,9 +123,25 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
         const BatchItem item = items[it];
         const BatchInst I = insts[item.inst];
         if (item.kind == 0) {
-            for (int first = item.a + w * 32; first < item.b; first += kBWarps * 32)
-                scatter_chunk32<false>(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, I.key, 0, I.SX, 0, s_rp[w],
-                                s_h[w], s_sg[w], bad);
+            // The item's row offsets and nonzeros into L2 first: each warp's loads are
+            // otherwise one DRAM round trip per 32 rows, which dominates very sparse
+            // instances (mostly empty rows).
+            if (t == 0) {
+                prefetch_l2_range(I.row_ptr + item.a, static_cast<size_t>(item.b - item.a + 1) * sizeof(int));
+                const int k0 = I.row_ptr[item.a], k1 = I.row_ptr[item.b];
+                if (0 <= k0 && k0 < k1 && k1 <= I.nnz) {
+                    prefetch_l2_range(I.col_idx + k0, static_cast<size_t>(k1 - k0) * sizeof(int));
+                    prefetch_l2_range(I.vals + k0, static_cast<size_t>(k1 - k0) * sizeof(float));
+                }
+            }
+            for (int first = item.a + w * 32; first < item.b; first += kBWarps * 32) {
+                if (I.lanes)  // warp-uniform
+                    scatter_lanes32<false, true>(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, 0,
+                                                 I.key, 0, I.SX, 0, bad);
+                else
+                    scatter_chunk32<false, true>(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, I.key,
+                                                 0, I.SX, 0, s_rp[w], s_h[w], s_sg[w], bad);
+            }
             __syncthreads();
             if (t == 0) {
                 __threadfence();
@@ -118,30 +175,30 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
                                     part, raw);
                 __syncthreads();
             }
+        // Two-level sum in a fixed order: the last item of each group of kSumGroup items
+        // adds the group's partials (in item order) into its group slot; the last group
+        // to finish adds the group slots (in group order) into Y.
+        const int md = I.m * I.d;
+        const int gamma = item.a / kSumGroup;
+        const int ngroups = (I.n_g + kSumGroup - 1) / kSumGroup;
+        const int g_lo = gamma * kSumGroup;
+        const int g_hi = min(I.n_g, g_lo + kSumGroup);
+        float *gslots = I.partials + static_cast<size_t>(I.part_cap) * md;
         if (t == 0) {
             __threadfence();
-            s_flag = atomicAdd(&g_done[item.inst], 1) == I.n_g - 1;
+            s_flag = atomicAdd(&grp_done[item.inst * kMaxGroups + gamma], 1) == g_hi - g_lo - 1;
         }
         __syncthreads();
-        if (s_flag) {  // the last contract item of the instance sums its partials in order
+        if (s_flag) {
             __threadfence();
-            // Four interleaved running sums (partials g = 0, 4, 8, ... into the first, and so
-            // on), then ((a0 + a1) + a2) + a3: a fixed order with four loads in flight.
-            const int md = I.m * I.d;
-            for (int o = t; o < md; o += kBThreads) {
-                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-                const float *p = I.partials + o;
-                int g = 0;
-                for (; g + 3 < I.n_g; g += 4) {
-                    a0 += __ldcg(p + static_cast<size_t>(g) * md);
-                    a1 += __ldcg(p + static_cast<size_t>(g + 1) * md);
-                    a2 += __ldcg(p + static_cast<size_t>(g + 2) * md);
-                    a3 += __ldcg(p + static_cast<size_t>(g + 3) * md);
-                }
-                if (g < I.n_g) a0 += __ldcg(p + static_cast<size_t>(g) * md);
-                if (g + 1 < I.n_g) a1 += __ldcg(p + static_cast<size_t>(g + 1) * md);
-                if (g + 2 < I.n_g) a2 += __ldcg(p + static_cast<size_t>(g + 2) * md);
-                I.Y[o] = ((a0 + a1) + a2) + a3;
+            sum_slots(I.partials, g_lo, g_hi, md, gslots + static_cast<size_t>(gamma) * md);
+            __threadfence();
+            __syncthreads();
+            if (t == 0) s_flag = atomicAdd(&g_done[item.inst], 1) == ngroups - 1;
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                sum_slots(gslots, 0, ngroups, md, I.Y);
             }
         }
         __syncthreads();
@@ -198,7 +255,7 @@ void build(cg_batch_plan &P) {
     P.part_off.assign(count, 0);
     size_t off = kStatusBytes;
     P.counters_off = off;
-    P.counters_bytes = (1 + 2 * static_cast<size_t>(count)) * sizeof(int);
+    P.counters_bytes = (1 + (2 + kMaxGroups) * static_cast<size_t>(count)) * sizeof(int);
     off += align256(P.counters_bytes);
     for (int k = 0; k < count; ++k) {
         P.sx_off[k] = off;
@@ -207,8 +264,8 @@ void build(cg_batch_plan &P) {
     P.zero_bytes = off - P.counters_off;
     for (int k = 0; k < count; ++k) {
         P.part_off[k] = off;
-        off += align256(static_cast<size_t>(max_contract_items(P.descs[k].B)) * P.descs[k].m * P.descs[k].d *
-                        sizeof(float));
+        off += align256(static_cast<size_t>(max_contract_items(P.descs[k].B) + kMaxGroups) * P.descs[k].m *
+                        P.descs[k].d * sizeof(float));
     }
     P.insts_off = off;
     off += align256(static_cast<size_t>(count) * sizeof(BatchInst));
@@ -227,18 +284,24 @@ void build(cg_batch_plan &P) {
         I.B = static_cast<uint32_t>(D.B);
         I.key = make_key(D.seed);
         const double per_row = D.n > 0 ? static_cast<double>(D.nnz) / static_cast<double>(D.n) : 1.0;
+        // rows per scatter item: about s_nnz nonzeros, but at most kMaxRowsPerItem rows, so
+        // that an item of a very sparse instance (mostly empty rows) stays short
         int64_t rows = pow2_floor(static_cast<int64_t>(static_cast<double>(P.s_nnz) / std::max(per_row, 1e-3)));
-        rows = std::max<int64_t>(32, std::min<int64_t>(rows, 1 << 20));
+        rows = std::max<int64_t>(32, std::min<int64_t>(rows, kMaxRowsPerItem));
         I.n_s = static_cast<int>((D.n + rows - 1) / rows);
         const int64_t nslabs = (D.B + kFfmaKT - 1) / kFfmaKT;
-        int64_t spg = (P.g_fma + static_cast<int64_t>(D.m) * D.d * kFfmaKT - 1) /
-                      (static_cast<int64_t>(D.m) * D.d * kFfmaKT);
+        // slabs per contract item: about g_fma "FMA-equivalents", counting each Gaussian
+        // drawn as kNormalCost FMAs (a Philox + Box-Muller quadruple is ~200 instructions)
+        const int64_t slab_cost = static_cast<int64_t>(D.m) * kFfmaKT * (D.d + kNormalCost);
+        int64_t spg = (P.g_fma + slab_cost - 1) / slab_cost;
         const int64_t cap = max_contract_items(D.B);
         spg = std::max<int64_t>(spg, (nslabs + cap - 1) / cap);
         spg = std::max<int64_t>(1, std::min(spg, nslabs));
         I.slabs_per_g = static_cast<int>(spg);
         I.n_g = static_cast<int>((nslabs + spg - 1) / spg);
+        I.part_cap = static_cast<int>(cap);
         I.rows_per_s = static_cast<int>(rows);
+        I.lanes = per_row < 1.0 ? 1 : 0;
     }
     for (int k : order) {
         const BatchInst &I = P.insts[k];
@@ -304,12 +367,13 @@ cudaError_t enqueue(cg_batch_plan &P, void *ws, cudaStream_t st) {
     int *head = reinterpret_cast<int *>(base + P.counters_off);
     int *s_done = head + 1;
     int *g_done = s_done + count;
+    int *grp_done = g_done + count;
     const int sms = num_sms() > 0 ? num_sms() : 148;
     const int grid = std::max(1, std::min<int>(sms * P.ctas_per_sm, static_cast<int>(P.items.size())));
     const long long cycles = static_cast<long long>(P.wait_us) * 2000;  // ~2 GHz SM clock
     batch_kernel<<<grid, kBThreads, 0, st>>>(reinterpret_cast<const BatchInst *>(base + P.insts_off),
                                             reinterpret_cast<const BatchItem *>(base + P.items_off),
-                                            static_cast<int>(P.items.size()), head, s_done, g_done, cycles,
+                                            static_cast<int>(P.items.size()), head, s_done, g_done, grp_done, cycles,
                                             reinterpret_cast<int *>(ws));
     return cudaGetLastError();
 }

@@ -70,7 +70,9 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, int F) {
 // column indices and malformed row offsets are skipped and reported through `bad`.  Only
 // rows whose bucket lies in [blo, bhi) are reduced (bucket-range passes); blo = 0,
 // bhi = B reduces every row.
-template <bool FIXED, int ROWS>
+// With SKIP_EMPTY, empty rows get no bucket and sign: a warp whose rows are all empty
+// skips the hash (worth it for inputs with mostly empty rows).
+template <bool FIXED, int ROWS, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                               const float *__restrict__ vals, int first, int n, int d, uint32_t B,
                                               int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
@@ -88,17 +90,24 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
         const int i = first + r * 32 + lane;
         rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
     }
+    if (SKIP_EMPTY) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) s_rp[r * 32 + lane] = rp[r];
+        if (lane == 0) s_rp[ROWS] = end;
+        __syncwarp();
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int i = first + r * 32 + lane;
         uint32_t h = 0;
         float sg = 0.0f;
-        if (i < n) hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
-        s_rp[r * 32 + lane] = rp[r];
+        if (i < n && (!SKIP_EMPTY || rp[r] < s_rp[r * 32 + lane + 1]))
+            hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+        if (!SKIP_EMPTY) s_rp[r * 32 + lane] = rp[r];
         s_h[r * 32 + lane] = h;
         s_sg[r * 32 + lane] = sg;
     }
-    if (lane == 0) s_rp[ROWS] = end;
+    if (!SKIP_EMPTY && lane == 0) s_rp[ROWS] = end;
     __syncwarp();
     const int beg = s_rp[0];
     bool ordered = true;
@@ -156,7 +165,7 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
 // row; the lanes' loads of one step fall in the chunk's short, contiguous range of
 // col_idx / vals (indexed from klo as in scatter_chunk).  Out-of-range column indices
 // and malformed row offsets are skipped and reported through `bad`.
-template <bool FIXED>
+template <bool FIXED, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                                 const float *__restrict__ vals, int first, int n, int d, uint32_t B,
                                                 int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
@@ -172,9 +181,9 @@ __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr,
             bad = 1;
             end = beg;
         }
-        uint32_t h;
-        float sg;
-        hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+        uint32_t h = 0;
+        float sg = 0.0f;
+        if (!SKIP_EMPTY || beg < end) hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
         if (h < blo || h >= bhi) end = beg;  // another pass reduces this row
         const size_t base = static_cast<size_t>(h) * d;
         for (int k = beg; k < end; ++k) {
@@ -194,13 +203,13 @@ __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr,
 }
 
 // The 32-row chunk (one row per lane).
-template <bool FIXED>
+template <bool FIXED, bool SKIP_EMPTY = false>
 __device__ __forceinline__ void scatter_chunk32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                                 const float *__restrict__ vals, int first, int n, int d, uint32_t B,
                                                 int nnz, Key key, int64_t row_offset, void *__restrict__ SX, int F,
                                                 int *s_rp, uint32_t *s_h, float *s_sg, int &bad) {
-    scatter_chunk<FIXED, 32>(row_ptr, col_idx, vals, first, n, d, B, nnz, 0, key, row_offset, SX, F, s_rp, s_h,
-                             s_sg, bad);
+    scatter_chunk<FIXED, 32, SKIP_EMPTY>(row_ptr, col_idx, vals, first, n, d, B, nnz, 0, key, row_offset, SX, F,
+                                         s_rp, s_h, s_sg, bad);
 }
 
 }  // namespace cg
