@@ -75,6 +75,7 @@ def _load():
                 "orc_adjoint_dense": [u64, i64, i64, i64, i64, i64, P, P, P],
                 "orc_adjoint_csr": [u64, i64, i64, i64, i64, i64, P, P, P, P, P],
                 "orc_row_argmax_argmin": [i64, i64, P, P, P],
+                "orc_apply_right_csr": [u64, i64, i64, i64, i64, i64, P, P, P, P],
             }
             for name, args in sigs.items():
                 fn = getattr(lib, name)
@@ -206,6 +207,17 @@ def apply_dense(seed, m, B, X, row_offset=0, return_sx=False):
     Y = np.zeros((m, d), np.float64)
     lib.orc_apply_dense(seed, n, d, m, B, row_offset, _ptr(X), _ptr(SX), _ptr(Y))
     return (Y, SX) if return_sx else Y
+
+
+def apply_right_csr(seed, n, d, m, B, row_ptr, col_idx, vals, col_offset=0) -> np.ndarray:
+    """Z = A.T^T, d x m float64, for a d x n CSR matrix A with one row per sample (the
+    projection X.R, R = T^T, of Section 9 and Table 1).  Column c of A is the global
+    index col_offset + c of T's columns."""
+    lib = _load()
+    rp, ci, v = _csr(row_ptr, col_idx, vals)
+    Z = np.zeros((d, m), np.float64)
+    lib.orc_apply_right_csr(seed, n, d, m, B, col_offset, _ptr(rp), _ptr(ci), _ptr(v), _ptr(Z))
+    return Z
 
 
 def plain_csr(seed, n, d, m, row_ptr, col_idx, vals, rows=None, row_offset=0) -> np.ndarray:

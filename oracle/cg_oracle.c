@@ -16,6 +16,8 @@
  *     (Section 2, Theorem 1).  No 1/sqrt(m) scaling is applied.
  *   - T = G.S and the product is computed as T.X = G.(S.X) (Section 1.1; Algorithm 1
  *     steps 1-2).  The plain product it replaces is G~.X (Abstract; Section 4).
+ *   - The SVM application projects a samples x features matrix X to X.R with
+ *     R = T^T (Section 9; Table 1 times this projection).
  *
  * What the paper leaves open and this project fixes (the "stream layout"):
  *   - Random words come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
@@ -243,6 +245,35 @@ void orc_apply_dense(uint64_t seed, int64_t n, int64_t d, int64_t m, int64_t B, 
 {
     orc_sketch_dense(seed, n, d, B, row_offset, X, SX);
     orc_contract(seed, m, B, d, SX, Y);
+}
+
+/* ---------------------------------------------------------------------------
+ * The random projection X.R of the SVM application (Section 9, the theorem on the
+ * margin; Table 1's "Proj" column), with R = T^T.  Here the data matrix A has one row
+ * per sample (d rows) and one column per feature (n columns), the orientation of
+ * Section 9, and Z = A.T^T is d x m.  Written from the definition T = G.S: column c
+ * of T is sigma(c) G[:, h(c)], so the nonzero A[r, c] adds A[r, c] sigma(c) G[:, h(c)]
+ * to row r of Z.  Column c of A carries the global index col_offset + c (the index
+ * T's column is drawn for).  Z is d x m row-major, overwritten.
+ * ------------------------------------------------------------------------- */
+void orc_apply_right_csr(uint64_t seed, int64_t n, int64_t d, int64_t m, int64_t B, int64_t col_offset,
+                         const int64_t *row_ptr, const int64_t *col_idx, const double *vals, double *Z)
+{
+    int64_t r, k, q;
+    double *g = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    (void)n;
+    memset(Z, 0, (size_t)(d * m) * sizeof(double));
+    for (r = 0; r < d; ++r) {
+        for (k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            int64_t h;
+            int s;
+            orc_hash_sign_one(seed, B, col_offset + col_idx[k], &h, &s);
+            orc_gauss_column(seed, ORC_TAG_G, m, h, g);
+            for (q = 0; q < m; ++q)
+                Z[r * m + q] += vals[k] * (double)s * g[q];
+        }
+    }
+    free(g);
 }
 
 /* ---------------------------------------------------------------------------

@@ -235,6 +235,46 @@ def test_brute_force_plain():
     assert rel(got, want[rows]) < 1e-13
 
 
+@pytest.mark.parametrize("n,d,m,B,seed", [(64, 5, 4, 32, 1), (50, 3, 7, 9, 2), (40, 1, 1, 1, 3),
+                                          (33, 8, 13, 64, 2**40 + 3)])
+def test_brute_force_right_projection(n, d, m, B, seed):
+    """Section 9's projection X.R with R = T^T: for a d x n matrix A (one row per
+    sample), Z = A.(G.S)^T with S and G materialised densely."""
+    A = synth.csr_ragged(d, n, seed=seed)
+    Ad = A.to_dense()
+    T = oracle.gaussian_G(seed, m, B) @ dense_S(seed, n, B)
+    Z = oracle.apply_right_csr(seed, n, d, m, B, A.row_ptr, A.col_idx, A.vals)
+    assert Z.shape == (d, m)
+    assert rel(Z, Ad @ T.T) < 1e-13
+
+
+def test_right_projection_is_transposed_left():
+    """A.T^T = (T.A^T)^T: the right form on A (T's columns added per nonzero) equals
+    the scatter-then-contract path on A^T, also with a global column offset."""
+    d, n, m, B, seed = 37, 300, 9, 45, 6
+    A = synth.csr_bernoulli(d, n, 0.05, seed=3)
+    At = synth.csr_from_dense(A.to_dense().T)
+    for off in (0, 1000):
+        Z = oracle.apply_right_csr(seed, n, d, m, B, A.row_ptr, A.col_idx, A.vals, col_offset=off)
+        Y = oracle.apply_csr(seed, n, d, m, B, At.row_ptr, At.col_idx, At.vals, row_offset=off)
+        assert rel(Z, Y.T) < 1e-13
+    Z0 = oracle.apply_right_csr(seed, n, d, m, B, A.row_ptr, A.col_idx, A.vals)
+    assert rel(Z, Z0) > 0.1  # the offset changes which columns of T are drawn
+
+
+def test_right_unit_matrix_reads_one_column_of_G():
+    """A = e_r e_c^T: row r of Z is sigma(c) G[:, h(c)] and every other row is 0."""
+    d, n, m, B, seed = 6, 40, 10, 17, 5
+    h, s = oracle.hash_sign(seed, B, 0, n)
+    G = oracle.gaussian_G(seed, m, B)
+    for r, c in [(0, 0), (3, 39), (5, 12)]:
+        rp = np.zeros(d + 1, np.int64)
+        rp[r + 1:] = 1
+        Z = oracle.apply_right_csr(seed, n, d, m, B, rp, np.array([c]), np.array([1.0]))
+        np.testing.assert_array_equal(Z[r], s[c] * G[:, h[c]])
+        assert not np.delete(Z, r, axis=0).any()
+
+
 def test_row_offset_is_global_index():
     """A shard with global row offset o uses h, sigma and G~ columns of rows o.. ;
     shard results sum to the unsharded one (distributed remark, Section 4)."""
