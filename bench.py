@@ -64,8 +64,8 @@ def parse_args():
     ap.add_argument("--reduction-sweep", action="store_true",
                     help="instead of the step: random fp32 reduction rate vs array size (the scatter's ceiling)")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
-    ap.add_argument("--rows", default="ladder,grad,batch,small",
-                    help="comma list of the other rows to measure (ladder, grad, batch, small)")
+    ap.add_argument("--rows", default="ladder,grad,batch,small,svm",
+                    help="comma list of the other rows to measure (ladder, grad, batch, small, svm)")
     return ap.parse_args()
 
 
@@ -245,10 +245,11 @@ def reduction_ceiling(dev, count, cells, reps=5):
             "how": "cg_diag_random_reductions: count fp32 adds at hashed positions of an SX-sized array"}
 
 
-def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small")):
+def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small", "svm")):
     """The other rows of the hot path, each on its own workload (sizes in synth.WORKLOADS):
     precision ladder and plain product on the largest workload, dense forward and
-    adjoint, the 96-instance batch, deterministic mode, and the small case's latency."""
+    adjoint, the 96-instance batch, deterministic mode, the small case's latency, and
+    the right projection of the SVM application on the largest TechTC-shaped pair."""
     import numpy as np
     import torch
 
@@ -267,6 +268,8 @@ def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small")):
         rows.update(_batch_row(dev, reps, csr_dev, stream))
     if "small" in which:
         rows.update(_small_row(dev, reps, csr_dev, stream))
+    if "svm" in which:
+        rows.update(_svm_row(dev, reps, csr_dev, stream))
     return rows
 
 
@@ -399,6 +402,56 @@ def _small_row(dev, reps, csr_dev, stream):
         "plain_python_call_us": 1e3 * _time_calls(lambda: plan.plain_csr(rp, ci, v, out=Yp), reps, stream)}
     plan.check()
     return rows
+
+
+def _svm_row(dev, reps, csr_dev, stream):
+    """The random projection X.R, R = T^T, of the SVM application (Section 9; Table 1
+    times it) on the largest TechTC-shaped pair (280 documents x 40,000 words, density
+    1e-2), for m = 128, 256, 512 with B = 5m: device time per projection (calls replayed
+    from a CUDA graph) in FP32 and BF16, the time of a call from Python, and end to end
+    from pinned host memory (CSR copied in, Z copied out, synchronised).  The plain
+    product G~.A^T on the same matrix where its kernel supports the shape."""
+    import numpy as np
+    import torch
+
+    from paper_1606_05732_gb300 import countgauss, synth
+    A = synth.techtc_pair(21, docs=280, words=40_000)
+    At = synth.csr_from_dense(A.to_dense().T)
+    rp, ci, v = csr_dev(A)
+    rpt, cit, vt = csr_dev(At)
+    host = [torch.from_numpy(a).pin_memory() for a in (A.row_ptr.astype(np.int32), A.col_idx, A.vals)]
+    dbuf = [torch.empty_like(h, device=dev) for h in host]
+    per_m = {}
+    for m in (128, 256, 512):
+        B = 5 * m
+        plan = countgauss.CountGauss(A.d, A.n, m, B, 21)
+        plan_bf = countgauss.CountGauss(A.d, A.n, m, B, 21, precision="bf16")
+        Z = torch.empty(A.n, m, dtype=torch.float32, device=dev)
+        Zh = torch.empty(A.n, m, dtype=torch.float32).pin_memory()
+
+        def e2e():
+            for h, dv in zip(host, dbuf):
+                dv.copy_(h, non_blocking=True)
+            plan.apply_right_csr(*dbuf, out=Z)
+            Zh.copy_(Z, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+
+        r = {"B": B,
+             "fp32_us": _graph_us(lambda: plan.apply_right_csr(rp, ci, v, out=Z), reps, dev),
+             "bf16_us": _graph_us(lambda: plan_bf.apply_right_csr(rp, ci, v, out=Z), reps, dev),
+             "python_call_us": 1e3 * _time_calls(lambda: plan.apply_right_csr(rp, ci, v, out=Z), reps, stream),
+             "e2e_host_us": 1e3 * _time_calls(e2e, reps, stream)}
+        Yp = torch.empty(m, A.n, dtype=torch.float32, device=dev)
+        try:
+            r["plain_us"] = _graph_us(lambda: plan.plain_csr(rpt, cit, vt, out=Yp), reps, dev)
+        except countgauss._lib.CountGaussError:
+            r["plain_us"] = None  # m x documents accumulator larger than the kernel's shared memory
+        plan.check()
+        plan_bf.check()
+        per_m[str(m)] = r
+    return {"svm_techtc_w40000_d280": {"docs": A.n, "words": A.d, "nnz": A.nnz, "density": 0.01,
+                                       "per_m": per_m,
+                                       "input": "synthetic TechTC-shaped pair (shape stand-in, not the dataset)"}}
 
 
 def run_ours(args):

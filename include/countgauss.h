@@ -131,7 +131,8 @@ typedef enum cg_op {
     CG_OP_PLAIN_CSR = 4,
     CG_OP_SKETCH = 5,         /* cg_sketch_csr / cg_sketch_dense alone */
     CG_OP_CONTRACT = 6,       /* cg_contract alone */
-    CG_OP_APPLY_CSR_HOST = 7  /* cg_apply_csr_host */
+    CG_OP_APPLY_CSR_HOST = 7, /* cg_apply_csr_host */
+    CG_OP_APPLY_RIGHT_CSR = 8 /* cg_apply_right_csr */
 } cg_op;
 
 /* ---- plans ---------------------------------------------------------------- */
@@ -185,6 +186,21 @@ CG_API cg_status cg_apply_dense(cg_plan *plan, const float *X, int64_t ldx, floa
 CG_API cg_status cg_apply_adjoint(cg_plan *plan, const float *dY, const int32_t *row_ptr,
                            const int32_t *col_idx, int64_t nnz, float *dX,
                            void *ws, size_t ws_bytes, void *stream);
+
+/* The random projection of the SVM application (Section 9, the theorem on the margin;
+ * Table 1 times it): Z = A.R with R = T^T, for a CSR matrix A with one row per sample
+ * and one column per feature, i.e. A = X^T in the plan's terms.  A has d rows and n
+ * columns: row_ptr int32[d+1] (row_ptr[0] = 0, row_ptr[d] = nnz), col_idx int32[nnz]
+ * in [0, n), vals fp32[nnz]; column c is T's column CG_OPT_ROW_OFFSET + c.  Computed
+ * as (G.(S.A^T))^T: the nonzero A[r, c] is reduced into SX[h(c), r] (B x d, in ws),
+ * then SX is contracted with G as in cg_apply_csr (CG_OPT_PRECISION applies) and the
+ * result stored transposed.  Z (device, d x m row-major) is overwritten.  Workspace:
+ * cg_workspace_size(CG_OP_APPLY_RIGHT_CSR, nnz).  Out-of-range column indices and
+ * out-of-range or decreasing row offsets are reported through the status word (the
+ * entries concerned are skipped).  CG_OPT_DETERMINISTIC = 1 gives CG_ERR_UNSUPPORTED. */
+CG_API cg_status cg_apply_right_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
+                                    const float *vals, int64_t nnz, float *Z,
+                                    void *ws, size_t ws_bytes, void *stream);
 
 /* The plain product Y = G~.X that the method replaces (Abstract; Section 4), with
  * the m x n Gaussian G~ generated on the fly, one column per non-empty row of X.

@@ -27,6 +27,7 @@ SCATTER = {"auto": 0, "atomic": 1, "partition": 2, "deferred": 3}
 KERNEL_SKETCH, KERNEL_CONTRACT, KERNEL_PLAIN, KERNEL_ADJOINT_W, KERNEL_GATHER = range(5)
 OP_APPLY_CSR, OP_APPLY_DENSE, OP_ADJOINT_DENSE, OP_ADJOINT_CSR, OP_PLAIN_CSR, OP_SKETCH, OP_CONTRACT = range(7)
 OP_APPLY_CSR_HOST = 7
+OP_APPLY_RIGHT_CSR = 8
 OPT_HOST_CHUNK = 10
 
 P = ctypes.c_void_p
@@ -42,6 +43,7 @@ SIGNATURES = {
     "cg_plan_check": [P, P, P],
     "cg_plan_timing": [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
     "cg_apply_csr": [P, P, P, P, I64, P, P, SZ, P],
+    "cg_apply_right_csr": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_csr_host": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_csr_noalloc": [P, P, P, P, I64, P, P],
     "cg_apply_dense": [P, P, I64, P, P, SZ, P],

@@ -136,6 +136,22 @@ class CountGauss:
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
         return Y
 
+    def apply_right_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
+        """Z = A.T^T (d x m) for a d x n CSR matrix A with one row per sample: the random
+        projection X.R, R = T^T, of the SVM application (Section 9; Table 1)."""
+        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        col_idx = _need(col_idx, torch.int32, "col_idx")
+        vals = _need(vals, torch.float32, "vals")
+        if row_ptr.numel() != self.d + 1:
+            raise ValueError(f"row_ptr must have d + 1 = {self.d + 1} entries (one row per sample)")
+        dev = row_ptr.device
+        nnz = col_idx.numel()
+        Z = torch.empty(self.d, self.m, dtype=torch.float32, device=dev) if out is None else out
+        ws = self.workspace(_lib.OP_APPLY_RIGHT_CSR, nnz, dev)
+        _lib.check("cg_apply_right_csr", self._lib.cg_apply_right_csr(
+            self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Z), _ptr(ws), ws.numel(), _stream(dev)))
+        return Z
+
     def apply_csr_host(self, row_ptr, col_idx, vals, out=None, device=None) -> torch.Tensor:
         """Y = G.(S.X) for a CSR X in host memory, Y returned in host memory
         (cg_apply_csr_host: chunked copies on a second stream overlap the scatter).

@@ -299,6 +299,11 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
         case CG_OP_SKETCH:
             L.c_bytes = scatter_scratch(p, nnz, &L.part);
             break;
+        case CG_OP_APPLY_RIGHT_CSR:
+            L.a_bytes = sx;
+            L.b_bytes = contract_partials_bytes(p);
+            L.c_bytes = right_scratch_bytes(p.n, nnz);
+            break;
         case CG_OP_APPLY_CSR_HOST: {
             const HostCaps c = host_caps(p, nnz);
             L.a_bytes = sx;
@@ -336,15 +341,16 @@ cg_status check_csr(const cg_plan *p, const int32_t *row_ptr, const int32_t *col
 int *status_word(void *ws) { return reinterpret_cast<int *>(ws); }
 char *region(void *ws, size_t off) { return reinterpret_cast<char *>(ws) + off; }
 
-cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const Layout &L, cudaStream_t st) {
+// Y = G.SX (m x d), or with `transpose` its transpose (d x m).
+cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const Layout &L, cudaStream_t st,
+                       bool transpose = false) {
     if (p->precision != CG_PREC_FP32)
         return from_cuda(launch_contract_tc(SX, p->m, p->d, p->B, make_key(p->seed), p->precision,
                                             contract_tc_splits(*p), reinterpret_cast<float *>(region(ws, L.b_off)),
-                                            Y, status_word(ws), timing_pair(p, CG_KERNEL_CONTRACT), st));
-    if (p->precision != CG_PREC_FP32) return CG_ERR_UNSUPPORTED;
+                                            Y, status_word(ws), timing_pair(p, CG_KERNEL_CONTRACT), st, transpose));
     return from_cuda(launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), contract_splits(*p),
                                           reinterpret_cast<float *>(region(ws, L.b_off)), Y,
-                                          timing_pair(p, CG_KERNEL_CONTRACT), st));
+                                          timing_pair(p, CG_KERNEL_CONTRACT), st, transpose));
 }
 
 cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
@@ -561,7 +567,7 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
 }
 
 cg_status cg_workspace_size(const cg_plan *p, int32_t op, int64_t nnz, size_t *bytes) {
-    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_APPLY_CSR_HOST) return CG_ERR_INVALID_ARG;
+    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_APPLY_RIGHT_CSR) return CG_ERR_INVALID_ARG;
     *bytes = layout_for(*p, op, nnz).total;
     return CG_OK;
 }
@@ -625,6 +631,23 @@ cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_id
     cudaStream_t st = as_stream(stream);
     if ((s = run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, L, st)) != CG_OK) return s;
     return run_contract(p, SX, Y, ws, L, st);
+}
+
+cg_status cg_apply_right_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                             int64_t nnz, float *Z, void *ws, size_t ws_bytes, void *stream) {
+    if (p == nullptr || Z == nullptr || misaligned(Z, 4)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
+    if (s != CG_OK) return s;
+    if (p->deterministic) return CG_ERR_UNSUPPORTED;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_APPLY_RIGHT_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    s = from_cuda(launch_right_scatter(row_ptr, col_idx, vals, p->d, p->n, static_cast<uint32_t>(p->B),
+                                       static_cast<int>(nnz), make_key(p->seed), p->row_offset, region(ws, L.c_off),
+                                       SX, status_word(ws), timing_pair(p, CG_KERNEL_SKETCH), st));
+    if (s != CG_OK) return s;
+    return run_contract(p, SX, Z, ws, L, st, true);
 }
 
 cg_status cg_apply_dense(cg_plan *p, const float *X, int64_t ldx, float *Y, void *ws, size_t ws_bytes,

@@ -36,40 +36,68 @@ contract_ffma_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key 
                           part + static_cast<size_t>(blockIdx.x) * m * d, raw);
 }
 
-// Y[o] = sum over s of part[s][o]: 32 outputs per CTA (lanes, coalesced), 32 warps
-// each summing every 32nd partial in increasing s, then the 32 warp sums in
-// increasing warp order -- a fixed order, so Y is reproducible for a given grid.
-constexpr int kRedWarps = 32;
+// Y[o] = sum over s of part[s][o], for groups of 32 consecutive outputs (the lanes of a
+// warp, coalesced).  W warps share a group: warp w sums the partials s = w, w + W, ...
+// in increasing s, then the W warp sums are added in increasing w -- a fixed order for
+// a given (nsplit, W), so Y is reproducible.  W follows nsplit (about four partials per
+// warp), so that few splits over many outputs do not leave most warps idle.  CTAs hold
+// 256 threads (8 / W groups) for W <= 8 and one group of W warps otherwise.  With
+// tr_cols > 0 the rows x tr_cols result is stored transposed: output o = q tr_cols + j
+// goes to Y[j (total / tr_cols) + q].
+template <int W>
+constexpr int red_threads() { return W >= 8 ? W * 32 : 256; }
 
-__global__ void __launch_bounds__(kRedWarps * 32)
-reduce_splits_kernel(const float *__restrict__ part, int nsplit, int64_t total, float *__restrict__ Y) {
-    __shared__ float red[kRedWarps][33];
+template <int W>
+__global__ void __launch_bounds__(red_threads<W>())
+reduce_splits_kernel(const float *__restrict__ part, int nsplit, int64_t total, int tr_cols, float *__restrict__ Y) {
+    constexpr int kGroups = red_threads<W>() / (32 * W);
+    __shared__ float red[W > 1 ? red_threads<W>() / 32 : 1][33];
     const int lane = threadIdx.x & 31;
-    const int sl = threadIdx.x >> 5;
-    const int64_t o = static_cast<int64_t>(blockIdx.x) * 32 + lane;
+    const int warp = threadIdx.x >> 5;
+    const int grp = warp / W;
+    const int sl = warp % W;
+    const int64_t o = (static_cast<int64_t>(blockIdx.x) * kGroups + grp) * 32 + lane;
     float acc = 0.0f;
     if (o < total) {
         int s = sl;
-        for (; s + 3 * kRedWarps < nsplit; s += 4 * kRedWarps) {
+        for (; s + 3 * W < nsplit; s += 4 * W) {
             const float a0 = __ldg(part + static_cast<size_t>(s) * total + o);
-            const float a1 = __ldg(part + static_cast<size_t>(s + kRedWarps) * total + o);
-            const float a2 = __ldg(part + static_cast<size_t>(s + 2 * kRedWarps) * total + o);
-            const float a3 = __ldg(part + static_cast<size_t>(s + 3 * kRedWarps) * total + o);
+            const float a1 = __ldg(part + static_cast<size_t>(s + W) * total + o);
+            const float a2 = __ldg(part + static_cast<size_t>(s + 2 * W) * total + o);
+            const float a3 = __ldg(part + static_cast<size_t>(s + 3 * W) * total + o);
             acc += a0;
             acc += a1;
             acc += a2;
             acc += a3;
         }
-        for (; s < nsplit; s += kRedWarps) acc += __ldg(part + static_cast<size_t>(s) * total + o);
+        for (; s < nsplit; s += W) acc += __ldg(part + static_cast<size_t>(s) * total + o);
     }
-    red[sl][lane] = acc;
-    __syncthreads();
-    if (sl == 0 && o < total) {
-        float r = red[0][lane];
+    float r = acc;
+    if (W > 1) {
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (sl != 0) return;
+        r = red[grp * W][lane];
 #pragma unroll
-        for (int q = 1; q < kRedWarps; ++q) r += red[q][lane];
-        Y[o] = r;
+        for (int q = 1; q < W; ++q) r += red[grp * W + q][lane];
     }
+    if (o < total) {
+        if (tr_cols > 0)
+            Y[(o % tr_cols) * (total / tr_cols) + o / tr_cols] = r;
+        else
+            Y[o] = r;
+    }
+}
+
+template <int W>
+cudaError_t launch_reduce_w(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream,
+                            int tr_cols) {
+    constexpr int kGroups = red_threads<W>() / (32 * W);
+    const int64_t groups = (total + 31) / 32;
+    const int64_t grid = (groups + kGroups - 1) / kGroups;
+    reduce_splits_kernel<W><<<static_cast<unsigned>(grid), red_threads<W>(), 0, stream>>>(partials, nsplit, total,
+                                                                                          tr_cols, Y);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -101,15 +129,20 @@ size_t contract_partials_bytes(const cg_plan &p) {
     return static_cast<size_t>(splits) * p.m * p.d * sizeof(float);
 }
 
-cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream) {
+cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream,
+                                 int tr_cols) {
     if (total == 0) return cudaSuccess;
-    const int64_t grid = (total + 31) / 32;
-    reduce_splits_kernel<<<static_cast<unsigned>(grid), kRedWarps * 32, 0, stream>>>(partials, nsplit, total, Y);
-    return cudaGetLastError();
+    const int per_warp = (nsplit + 3) / 4;  // warps per group: about four partials each
+    if (per_warp <= 1) return launch_reduce_w<1>(partials, nsplit, total, Y, stream, tr_cols);
+    if (per_warp <= 2) return launch_reduce_w<2>(partials, nsplit, total, Y, stream, tr_cols);
+    if (per_warp <= 4) return launch_reduce_w<4>(partials, nsplit, total, Y, stream, tr_cols);
+    if (per_warp <= 8) return launch_reduce_w<8>(partials, nsplit, total, Y, stream, tr_cols);
+    if (per_warp <= 16) return launch_reduce_w<16>(partials, nsplit, total, Y, stream, tr_cols);
+    return launch_reduce_w<32>(partials, nsplit, total, Y, stream, tr_cols);
 }
 
 cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials,
-                                 float *Y, const EventPair *ev, cudaStream_t stream) {
+                                 float *Y, const EventPair *ev, cudaStream_t stream, bool transpose) {
     const int64_t nslabs = (B + kKT - 1) / kKT;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
@@ -126,7 +159,7 @@ cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key k
     record(ev, false, stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream);
+    return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream, transpose ? d : 0);
 }
 
 }  // namespace cg

@@ -584,7 +584,8 @@ int contract_tc_splits(const cg_plan &p) {
 }
 
 cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
-                               float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream) {
+                               float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream,
+                               bool transpose) {
     cudaError_t e;
     const bool fp8 = precision == CG_PREC_FP8_E4M3 || precision == CG_PREC_FP8X3;
     const int nt = fp8 ? tc8_nt(d) : tc_nt(d);
@@ -610,7 +611,7 @@ cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key
     const int64_t nslabs = (B + bk - 1) / bk;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
-    return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream);
+    return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream, transpose ? d : 0);
 }
 
 }  // namespace cg

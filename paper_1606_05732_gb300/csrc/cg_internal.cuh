@@ -112,16 +112,30 @@ cudaError_t launch_sketch_csr_partitioned(const int *row_ptr, const int *col_idx
                                           cudaStream_t stream);
 
 // ---- contraction (cg_gauss.cu) ----------------------------------------------
+// Y = G.SX (m x d row-major), or with `transpose` its transpose (d x m row-major).
 int contract_splits(const cg_plan &p);
 size_t contract_partials_bytes(const cg_plan &p);
 cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials,
-                                 float *Y, const EventPair *ev, cudaStream_t stream);
-cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream);
+                                 float *Y, const EventPair *ev, cudaStream_t stream, bool transpose = false);
+// Y = fixed-order sum of nsplit partials of `total` floats; with tr_cols > 0 the
+// (total / tr_cols) x tr_cols result is stored transposed.
+cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream,
+                                 int tr_cols = 0);
 
 // ---- tensor-core contraction (cg_gauss_tc.cu) -----------------------------------
 int contract_tc_splits(const cg_plan &p);
 cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
-                               float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream);
+                               float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream,
+                               bool transpose = false);
+
+// ---- right projection Z = A.T^T (cg_right.cu) -------------------------------------
+// Scratch bytes of the scatter of a rows x n CSR matrix with nnz nonzeros (the table of
+// column codes, when it pays), and the scatter SX[h(c), r] += sigma(c) A[r, c] itself
+// (SX is B x rows, cleared here).
+size_t right_scratch_bytes(int64_t n, int64_t nnz);
+cudaError_t launch_right_scatter(const int *row_ptr, const int *col_idx, const float *vals, int rows, int64_t n,
+                                 uint32_t B, int nnz, Key key, int64_t col_offset, void *scratch, float *SX,
+                                 int *status, const EventPair *ev, cudaStream_t stream);
 
 // ---- plain product (cg_plain.cu) ---------------------------------------------
 bool plain_supported(int m, int d);

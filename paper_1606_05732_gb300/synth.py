@@ -15,6 +15,9 @@ densities and value distributions of the benchmark configurations:
   input, Section 3.1 of the paper), float32.
 * ``dense_normal``: dense n x d N(0,1) float32.
 * ``batch_instances``: the 96 uneven instances of the batched workload.
+* ``techtc_pair``: a documents x words matrix shaped like one TechTC-300 pair of
+  the SVM experiments (150-280 documents, 10,000-40,000 words); a shape stand-in,
+  not the dataset.
 """
 from __future__ import annotations
 
@@ -112,6 +115,18 @@ def csr_ragged(n: int, d: int, seed: int, empty_frac: float = 0.3, max_row: int 
             cols[row_ptr[i]:row_ptr[i + 1]] = rng.choice(d, size=L, replace=False)
     vals = rng.standard_normal(cols.size, dtype=np.float32)
     return CSR(n, d, row_ptr, cols, vals)
+
+
+def techtc_pair(seed: int, docs: int | None = None, words: int | None = None, density: float = 1e-2) -> CSR:
+    """Documents x words CSR (one row per document) shaped like one TechTC-300 pair of
+    the SVM experiments (Section 5: 150-280 documents, 10,000-40,000 words), with the
+    sizes drawn uniformly unless given.  The paper states no density; 1e-2 is taken.
+    Nonnegative term weights U[0,1) on an i.i.d. Bernoulli pattern.  A shape stand-in,
+    not the dataset."""
+    rng = np.random.default_rng(seed)
+    docs = int(rng.integers(150, 281)) if docs is None else docs
+    words = int(rng.integers(10_000, 40_001)) if words is None else words
+    return csr_bernoulli(docs, words, density, seed=seed + 1, values="uniform")
 
 
 def dense_normal(n: int, d: int, seed: int) -> np.ndarray:

@@ -83,7 +83,7 @@ def test_options_and_workspace(lib):
         for x in bad:
             assert lib.cg_plan_set_option(h, opt, x) == 1
     sz = ctypes.c_size_t()
-    for op in range(7):
+    for op in range(9):
         assert lib.cg_workspace_size(h, op, 1000, ctypes.byref(sz)) == 0
         assert sz.value >= 256 and sz.value % 256 == 0
     assert lib.cg_workspace_size(h, 42, 0, ctypes.byref(sz)) == 1
@@ -111,6 +111,28 @@ def test_host_side_argument_errors_launch_nothing(lib):
     assert lib.cg_generate_words(1, 0, 0, -5, fake, P(0)) == 1
     assert lib.cg_generate_gaussian(1, 1, 8, 4, 2, 0, 3, fake, P(0)) == 1
     assert lib.cg_plan_check(None, fake, P(0)) == 1
+    # the right projection: null Z, bad nnz, small workspace; deterministic mode unsupported
+    assert lib.cg_apply_right_csr(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_right_csr(h, fake, fake, fake, -3, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_right_csr(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
+    assert lib.cg_plan_set_option(h, 2, 1) == 0
+    assert lib.cg_apply_right_csr(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
+    lib.cg_plan_destroy(h)
+
+
+def test_right_projection_workspace_holds_column_table(lib):
+    """The right projection's workspace adds 4 bytes per column of A once the nonzeros
+    hash every column more than four times on average (the per-column code table)."""
+    n = 1000
+    st, h = _plan(lib, n=n, d=300, m=128, B=640)
+    sz = ctypes.c_size_t()
+    sizes = {}
+    for nnz in (0, 4 * n, 4 * n + 1):
+        assert lib.cg_workspace_size(h, 8, nnz, ctypes.byref(sz)) == 0
+        sizes[nnz] = sz.value
+    assert sizes[0] == sizes[4 * n]
+    assert sizes[4 * n + 1] - sizes[4 * n] >= 4 * n
+    assert sizes[0] >= 256 + 640 * 300 * 4
     lib.cg_plan_destroy(h)
 
 
