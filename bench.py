@@ -63,6 +63,8 @@ def parse_args():
                     help="nonzeros per chunk of the end-to-end host-input call (0: automatic)")
     ap.add_argument("--reduction-sweep", action="store_true",
                     help="instead of the step: random fp32 reduction rate vs array size (the scatter's ceiling)")
+    ap.add_argument("--kl-sweep", action="store_true",
+                    help="instead of the step: Theorem 1's KL / Pinsker bound and Lemma 5's distinguisher vs B")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
     ap.add_argument("--rows", default="ladder,grad,batch,small,svm",
                     help="comma list of the other rows to measure (ladder, grad, batch, small, svm)")
@@ -663,10 +665,40 @@ def reduction_sweep():
     print(json.dumps({"reduction_sweep": out, "count": count}))
 
 
+def kl_sweep():
+    """One JSON line: Theorem 1's distance bound measured on the device's sketches.  For a
+    2^20 x 16 matrix with orthonormal columns and m = 32, over 64 CountSketches per B:
+    KL(N(0, I) || N(0, U^T S^T S U)) (Claim 3), ||M - I||_F^2 against its closed form,
+    and Pinsker's bound on the distance of the m rows, for B / (d^2 m) from 1/8 to 64.
+    Then Lemma 5's distinguisher (block matrix, d = 8, m = 1024) at B = 256 (L = 2,
+    B = d^2 m / 256) and at B = 4 d^2 m (L = 64): the fraction of draws whose pair-norm
+    statistic for T.U exceeds the 99th percentile of the plain product's.  m is large so
+    that the chi-square noise of a pair norm (about 2 sqrt(2 / m)) stays below the 2/L
+    shift that a collision between two blocks causes."""
+    import numpy as np
+    import torch
+
+    from paper_1606_05732_gb300 import diagnostics
+    torch.cuda.set_device(0)
+    d, m = 16, 32
+    U = diagnostics.spread_orthonormal_csr(1 << 20, d)
+    Bs = [d * d * m // 8 * (4 ** k) for k in range(6)]
+    sweep = diagnostics.kl_sweep(U, m, Bs, range(64))
+    lem = []
+    for B in (256, 4 * 8 * 8 * 1024):
+        r = diagnostics.lemma5_experiment(8, 1024, B, range(200))
+        thr = float(np.quantile(r["plain"], 0.99))
+        lem.append({"B": B, "L": r["L"], "B_over_d2m": B / (8 * 8 * 1024),
+                    "detect_rate": float(np.mean(r["countgauss"] > thr)), "plain_p99": thr})
+    print(json.dumps({"kl_sweep": sweep, "d": d, "m": m, "n": U.n, "lemma5": lem}))
+
+
 def main():
     args = parse_args()
     if args.reduction_sweep:
         reduction_sweep()
+    elif args.kl_sweep:
+        kl_sweep()
     elif args.impl == "reference":
         run_reference(args)
     else:
