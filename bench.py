@@ -15,9 +15,10 @@ Printed JSON line (rank 0):
                  (8 nnz + 4 (n+1) + 4 B d) over its CUDA-event duration, against the
                  measured HBM copy bandwidth
   plain          the plain G~.X on the same input and GPU, and the speedup over it
-  e2e            the same metric through cg_apply_csr_host: the CSR in pinned host memory,
+  e2e            the same metric through cg_apply_csr_host: the CSR in pinned host memory
                  copied host->device in chunks that overlap the scatter, Y read back
-                 every step, through the same public call
+                 every step, through the same public call; copied_ms and direct_ms time
+                 the chunked copies and the scatter reading host memory in place
   cpu_baseline   the FP64 oracle on this machine's host cores (rank 0, N = 1)
 
 --impl reference times that oracle instead (the reference arm).
@@ -564,7 +565,8 @@ def run_ours(args):
 
     # end to end through the host-input call: H2D of the CSR, apply, D2H of Y, every step
     # (cg_apply_csr_host: the CSR in pinned host memory is copied in chunks on a second
-    # stream while earlier chunks are scattered; Y comes back to host memory)
+    # stream while earlier chunks are scattered, or read in place by the scatter; Y comes
+    # back to host memory)
     Y_h = torch.empty(m, d, dtype=torch.float32).pin_memory()
     plan.set_host_chunk(args.host_chunk)
 
@@ -590,6 +592,19 @@ def run_ours(args):
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_ms = float(t.item())
+    e2e_modes = {}  # the two ways of reading the host CSR, each forced (this rank's time)
+    for mode in ("copied", "direct"):
+        plan.set_host_read(mode)
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        q0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_modes[mode + "_ms"] = q0.elapsed_time(q1) / e2e_steps
+    plan.set_host_read("auto")
     h2d = int(rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 4)
     d2h = int(m * d * 4)
 
@@ -635,7 +650,8 @@ def run_ours(args):
             "plain": {"ms_per_step": plain_ms, "value": world * nnz / (plain_ms / 1e3), "unit": UNIT,
                       "speedup_countgauss_over_plain": plain_ms / ms_step},
             "e2e": {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "cg_apply_csr_host"},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "cg_apply_csr_host",
+                    "host_read": "auto", **e2e_modes},
             # per step: the scatter (two kernels when deferred, three when partitioned), the
             # contraction and its split-K sum
             "gpu_launches": (4 if deferred else (5 if partitioned else 3)) * args.steps,

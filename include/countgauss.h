@@ -109,9 +109,15 @@ typedef enum cg_option {
                                  average), 32, 64, 128 forced (rows staged in shared memory,
                                  nonzeros swept 32 at a time), or 1 (one row per lane, each
                                  lane walking its own row) */
-    CG_OPT_HOST_CHUNK = 10    /* cg_apply_csr_host: most nonzeros, and most rows, per chunk copied
+    CG_OPT_HOST_CHUNK = 10,   /* cg_apply_csr_host: most nonzeros, and most rows, per chunk copied
                                  to the device; 0 = automatic (nnz / 4 within [2^20, 2^24]), else
                                  32 .. 2^30 */
+    CG_OPT_HOST_READ = 11     /* cg_apply_csr_host: how the kernels get the host CSR.  0 = automatic
+                                 (copied), 1 = copied in chunks by the copy engine, 2 = direct: the
+                                 scatter kernel reads the host arrays in place over the CPU-GPU
+                                 link (no chunk-size limit on rows, no staging).  Direct reads need
+                                 all three arrays in page-locked memory mapped into the device's
+                                 address space; otherwise the call copies in chunks. */
 } cg_option;
 
 typedef enum cg_kernel {
@@ -356,7 +362,9 @@ CG_API cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, in
                                int64_t c0, int64_t c1, float *out, void *stream);
 
 /* Y = T.X (as cg_apply_csr) for a CSR X held in HOST memory, with Y written to HOST
- * memory: the end-to-end form, for callers whose data live on the host.  The rows are
+ * memory: the end-to-end form, for callers whose data live on the host.  With direct
+ * reads (CG_OPT_HOST_READ), the scatter kernel streams the page-locked host arrays
+ * itself over the CPU-GPU link and nothing is staged.  Otherwise the rows are
  * cut into chunks of at most CG_OPT_HOST_CHUNK nonzeros and rows (boundaries found by
  * binary search on the host row_ptr before anything is enqueued); an internal copy
  * stream copies chunk c + 1 into one of two staging buffers of the workspace while chunk

@@ -29,6 +29,8 @@ OP_APPLY_CSR, OP_APPLY_DENSE, OP_ADJOINT_DENSE, OP_ADJOINT_CSR, OP_PLAIN_CSR, OP
 OP_APPLY_CSR_HOST = 7
 OP_APPLY_RIGHT_CSR = 8
 OPT_HOST_CHUNK = 10
+OPT_HOST_READ = 11
+HOST_READ = {"auto": 0, "copied": 1, "direct": 2}
 
 P = ctypes.c_void_p
 I32, I64, U32, U64, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t

@@ -177,6 +177,11 @@ class CountGauss:
         """Most nonzeros and rows per chunk of apply_csr_host (CG_OPT_HOST_CHUNK; 0: automatic)."""
         self.set_option(_lib.OPT_HOST_CHUNK, int(nnz_per_chunk))
 
+    def set_host_read(self, mode: str) -> None:
+        """How apply_csr_host gets the host CSR (CG_OPT_HOST_READ): "auto", "copied" (chunked
+        copies by the copy engine) or "direct" (the scatter reads pinned host memory in place)."""
+        self.set_option(_lib.OPT_HOST_READ, _lib.HOST_READ[mode])
+
     def apply_dense(self, X, out=None) -> torch.Tensor:
         """Y = G.(S.X) for dense row-major X (n x d)."""
         X = _need(X, torch.float32, "X")

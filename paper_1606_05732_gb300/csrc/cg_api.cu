@@ -305,10 +305,12 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
             L.c_bytes = right_scratch_bytes(p.n, nnz);
             break;
         case CG_OP_APPLY_CSR_HOST: {
+            // [Y, m x d][two staging buffers (copied reads) or the scatter's scratch (direct reads)]
             const HostCaps c = host_caps(p, nnz);
             L.a_bytes = sx;
             L.b_bytes = contract_partials_bytes(p);
-            L.c_bytes = 2 * c.stage_bytes + static_cast<size_t>(p.m) * p.d * sizeof(float);
+            L.c_bytes = align256(static_cast<size_t>(p.m) * p.d * sizeof(float)) +
+                        std::max(2 * c.stage_bytes, scatter_scratch(p, nnz, &L.part));
             break;
         }
         default:
@@ -376,6 +378,44 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
                                               static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
                                               p->row_offset, SX, status_word(ws), static_cast<int>(p->sketch_ctas),
                                               p->scatter_passes, p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st));
+}
+
+// Device address of the page-locked host range [p, p + bytes), or nullptr when the
+// range is not page-locked memory mapped into the current device's address space.
+const void *mapped_host(const void *p, size_t bytes) {
+    if (p == nullptr || bytes == 0) return p;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return nullptr;
+    cudaPointerAttributes b;  // the last byte must lie in the same mapped allocation
+    if (cudaPointerGetAttributes(&b, static_cast<const char *>(p) + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost ||
+        static_cast<const char *>(b.devicePointer) != static_cast<const char *>(a.devicePointer) + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
+// Direct reads for cg_apply_csr_host: on request (CG_OPT_HOST_READ = 2), and only when
+// all three host arrays are mapped page-locked memory; then *drp, *dci, *dv receive their
+// device addresses.  Not the default: on GB300 over NVLink-C2C the scatter reading host
+// memory in place moves the CSR at about 177 GB/s, the copy engine at about 200 GB/s.
+bool host_read_direct(const cg_plan &p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                      int64_t nnz, const int32_t **drp, const int32_t **dci, const float **dv) {
+    if (p.host_read != 2) return false;
+    const void *a = mapped_host(row_ptr, static_cast<size_t>(p.n + 1) * sizeof(int32_t));
+    const void *b = mapped_host(col_idx, static_cast<size_t>(nnz) * sizeof(int32_t));
+    const void *c = mapped_host(vals, static_cast<size_t>(nnz) * sizeof(float));
+    if (a == nullptr || (nnz > 0 && (b == nullptr || c == nullptr))) return false;
+    *drp = static_cast<const int32_t *>(a);
+    *dci = static_cast<const int32_t *>(b);
+    *dv = static_cast<const float *>(c);
+    return true;
 }
 
 // Copy stream and events of cg_apply_csr_host, made on first use on a device and kept
@@ -463,6 +503,7 @@ cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t se
     p->scatter_passes = 0;
     p->scatter_rows = 0;
     p->host_chunk = 0;
+    p->host_read = 0;
     p->host_state = nullptr;
     *out = p;
     return CG_OK;
@@ -544,6 +585,10 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             if (value != 0 && (value < 32 || value > (1LL << 30))) return CG_ERR_INVALID_ARG;
             p->host_chunk = value;
             return CG_OK;
+        case CG_OPT_HOST_READ:
+            if (value < 0 || value > 2) return CG_ERR_INVALID_ARG;
+            p->host_read = static_cast<int32_t>(value);
+            return CG_OK;
         default:
             return CG_ERR_INVALID_ARG;
     }
@@ -562,6 +607,7 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
         case CG_OPT_SCATTER_PASSES: *value = p->scatter_passes; return CG_OK;
         case CG_OPT_SCATTER_ROWS: *value = p->scatter_rows; return CG_OK;
         case CG_OPT_HOST_CHUNK: *value = p->host_chunk; return CG_OK;
+        case CG_OPT_HOST_READ: *value = p->host_read; return CG_OK;
         default: return CG_ERR_INVALID_ARG;
     }
 }
@@ -736,12 +782,26 @@ cg_status cg_apply_csr_host(cg_plan *p, const int32_t *row_ptr, const int32_t *c
     if (p->deterministic || use_partition(*p)) return CG_ERR_UNSUPPORTED;
     Layout L;
     if ((s = check_ws(p, CG_OP_APPLY_CSR_HOST, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
-    const HostCaps caps = host_caps(*p, nnz);
     const int64_t n = p->n;
+    cudaStream_t st = as_stream(stream);
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    float *Yd = reinterpret_cast<float *>(region(ws, L.c_off));
+    Layout Lrest = L;  // region C past Y: staging buffers, or the scatter's scratch
+    Lrest.c_off = L.c_off + align256(static_cast<size_t>(p->m) * p->d * sizeof(float));
+    if (row_ptr[0] < 0 || row_ptr[n] > nnz || row_ptr[0] > row_ptr[n]) return CG_ERR_INVALID_ARG;
+    const int32_t *drp = nullptr, *dci = nullptr;
+    const float *dv = nullptr;
+    if (host_read_direct(*p, row_ptr, col_idx, vals, nnz, &drp, &dci, &dv)) {
+        // the kernels stream the host arrays in place (offsets checked on the device)
+        if ((s = run_sketch_csr(p, drp, dci, dv, nnz, SX, ws, Lrest, st)) != CG_OK) return s;
+        if ((s = run_contract(p, SX, Yd, ws, L, st)) != CG_OK) return s;
+        return from_cuda(cudaMemcpyAsync(Y, Yd, static_cast<size_t>(p->m) * p->d * sizeof(float),
+                                         cudaMemcpyDeviceToHost, st));
+    }
+    const HostCaps caps = host_caps(*p, nnz);
     // Chunk boundaries [r0, r1): the most rows (at most caps.rows) whose nonzeros
     // row_ptr[r0] .. row_ptr[r1] number at most caps.nnz, by binary search.
     std::vector<int64_t> cuts{0};
-    if (row_ptr[0] < 0 || row_ptr[n] > nnz || row_ptr[0] > row_ptr[n]) return CG_ERR_INVALID_ARG;
     for (int64_t r0 = 0; r0 < n;) {
         const int64_t k0 = row_ptr[r0];
         auto fits = [&](int64_t r) { return row_ptr[r] >= k0 && row_ptr[r] - k0 <= caps.nnz && row_ptr[r] <= nnz; };
@@ -756,10 +816,7 @@ cg_status cg_apply_csr_host(cg_plan *p, const int32_t *row_ptr, const int32_t *c
     }
     HostState *h = host_state(p);
     if (h == nullptr) return CG_ERR_CUDA;
-    cudaStream_t st = as_stream(stream);
-    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
-    char *stage0 = region(ws, L.c_off);
-    float *Yd = reinterpret_cast<float *>(stage0 + 2 * caps.stage_bytes);
+    char *stage0 = region(ws, Lrest.c_off);
     const Key key = make_key(p->seed);
     if (cudaMemsetAsync(SX, 0, static_cast<size_t>(p->B) * p->d * sizeof(float), st) != cudaSuccess) return CG_ERR_CUDA;
     // The copies start after earlier work on `stream` and after the staging buffers'

@@ -25,6 +25,7 @@ struct cg_plan {
     int32_t scatter_passes; // CG_OPT_SCATTER_PASSES (0 = auto)
     int32_t scatter_rows;   // CG_OPT_SCATTER_ROWS (0 = auto)
     int64_t host_chunk;     // CG_OPT_HOST_CHUNK (0 = auto)
+    int32_t host_read;      // CG_OPT_HOST_READ (0 = auto, 1 = copied, 2 = direct)
     void *host_state;       // copy stream and events of cg_apply_csr_host, created on first use
 };
 

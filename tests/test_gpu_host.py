@@ -62,6 +62,50 @@ def test_host_apply_matches_oracle(n, d, m, B, seed, kind, chunk):
     assert rel(Y, Yo) < FP32_TOL
 
 
+@pytest.mark.parametrize("n,d,m,B,seed,kind,chunk", CASES[::2])
+@pytest.mark.parametrize("mode", ["direct", "copied"])
+def test_host_read_modes_match_oracle(n, d, m, B, seed, kind, chunk, mode):
+    """Direct reads (the scatter streams the pinned host arrays in place) and chunked
+    copies give the oracle's result."""
+    X = make(n, d, seed, kind)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    plan.set_host_read(mode)
+    plan.set_host_chunk(chunk)
+    Y = plan.apply_csr_host(*host_csr(X)).numpy()
+    plan.check()
+    assert rel(Y, oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals)) < FP32_TOL
+
+
+def test_host_direct_read_fallbacks_and_errors():
+    """Direct reads asked for pageable arrays fall back to copies; a sub-range of a
+    pinned buffer is read in place; malformed offsets are still caught (at the ends on
+    the host, inside on the device)."""
+    from paper_1606_05732_gb300 import _lib
+    n, d, m, B, seed = 30000, 32, 16, 1024, 9
+    X = synth.csr_bernoulli(n, d, 0.05, seed=seed)
+    want = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    plan.set_host_read("direct")
+    assert rel(plan.apply_csr_host(*host_csr(X, pin=False)).numpy(), want) < FP32_TOL
+    rp, ci, v = host_csr(X)
+    big = torch.zeros(X.nnz + 64, dtype=torch.float32).pin_memory()
+    big[64:] = v
+    assert rel(plan.apply_csr_host(rp, ci, big[64:]).numpy(), want) < FP32_TOL
+    plan.check()
+    bad = rp.clone()
+    bad[-1] = X.nnz + 5
+    with pytest.raises(_lib.CountGaussError) as e:
+        plan.apply_csr_host(bad.pin_memory(), ci, v)
+    assert e.value.status == _code("CG_ERR_INVALID_ARG")
+    bad = rp.clone()
+    bad[500], bad[501] = rp[501].item(), rp[500].item()
+    plan.apply_csr_host(bad.pin_memory(), ci, v)
+    with pytest.raises(_lib.CountGaussError) as e:
+        plan.check()
+    assert e.value.status == _code("CG_ERR_DEVICE_BOUNDS")
+    plan.check()
+
+
 def test_host_apply_repeats_and_matches_device_path():
     """Two calls in a row (the staging buffers reused), pageable inputs as well, and
     the device-input path: all within fp32 reduction-order rounding of each other."""
@@ -87,13 +131,18 @@ def test_host_apply_errors():
     n, d, m, B, seed = 1000, 8, 4, 64, 2
     X = synth.csr_bernoulli(n, d, 0.5, seed=seed)
     rp, ci, v = host_csr(X)
-    # a row longer than the chunk
+    # a row longer than the chunk: unsupported when copied in chunks, fine when read in place
     Xl = synth.csr_ragged(100, 64, seed=3, max_row=64)  # has a full 64-entry row
     long_rows = cg().CountGauss(100, 64, m, B, seed)
     long_rows.set_host_chunk(32)
+    long_rows.set_host_read("copied")
     with pytest.raises(_lib.CountGaussError) as e:
         long_rows.apply_csr_host(*host_csr(Xl))
     assert e.value.status == _code("CG_ERR_UNSUPPORTED")
+    long_rows.set_host_read("direct")
+    Yl = long_rows.apply_csr_host(*host_csr(Xl)).numpy()
+    long_rows.check()
+    assert rel(Yl, oracle.apply_csr(seed, 100, 64, m, B, Xl.row_ptr, Xl.col_idx, Xl.vals)) < FP32_TOL
     # deterministic plans are not supported
     det = cg().CountGauss(n, d, m, B, seed, deterministic=True)
     with pytest.raises(_lib.CountGaussError) as e:
