@@ -29,7 +29,8 @@ bool uses_table(int64_t n, int64_t nnz) { return n > 0 && nnz > kTableRepeats * 
 // h leaves the top bit free).
 __global__ void __launch_bounds__(kRightThreads)
 column_codes_kernel(Key key, int64_t col_offset, int n, uint32_t B, uint32_t *__restrict__ codes) {
-    for (int c = blockIdx.x * kRightThreads + threadIdx.x; c < n; c += gridDim.x * kRightThreads) {
+    for (int64_t c = static_cast<int64_t>(blockIdx.x) * kRightThreads + threadIdx.x; c < n;
+         c += static_cast<int64_t>(gridDim.x) * kRightThreads) {
         uint32_t h;
         float s;
         hash_sign(key, static_cast<uint64_t>(col_offset + c), B, h, s);
