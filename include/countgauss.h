@@ -32,7 +32,8 @@
  *   - Dense matrices are row-major fp32.  Y is m x d, SX is B x d, W is B x d.
  *   - CSR X: row_ptr int32[n+1] with row_ptr[0] = 0 and row_ptr[n] = nnz,
  *     col_idx int32[nnz] in [0, d) (any order within a row; duplicates are summed),
- *     vals fp32[nnz].  nnz < 2^31.
+ *     vals fp32[nnz].  nnz <= 2^31 - 2^20 (the margin keeps the kernels' 32-bit
+ *     indices from overflowing as they step past the last entry).
  *   - ws is a device workspace of at least cg_workspace_size() bytes, 256-byte
  *     aligned.  Its first 256 bytes hold a device status word that the kernels set
  *     when a bounds check fails (the offending element is skipped, never accessed)

@@ -332,7 +332,7 @@ cg_status check_ws(const cg_plan *p, int op, int64_t nnz, void *ws, size_t ws_by
 
 cg_status check_csr(const cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                     int64_t nnz, bool need_vals) {
-    if (nnz < 0 || nnz > 0x7fffffffLL) return CG_ERR_INVALID_ARG;
+    if (nnz < 0 || nnz > kMaxNnz) return CG_ERR_INVALID_ARG;
     if (row_ptr == nullptr) return CG_ERR_INVALID_ARG;
     if (nnz > 0 && (col_idx == nullptr || (need_vals && vals == nullptr))) return CG_ERR_INVALID_ARG;
     if (misaligned(row_ptr, 4) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;

@@ -51,6 +51,11 @@ constexpr int kStatusTimeout = 2;
 
 constexpr size_t kStatusBytes = 256;
 
+// Most stored entries of a CSR input: below 2^31 by a margin, so that the kernels' 32-bit
+// nonzero indices never overflow when they step past the last entry (by at most a few
+// thousand per step).
+constexpr int64_t kMaxNnz = (1LL << 31) - (1LL << 20);
+
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 // SM count of the current device (cached per device).  Returns 0 without a device.

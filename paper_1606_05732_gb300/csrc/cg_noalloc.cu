@@ -55,7 +55,7 @@ extern "C" cg_status cg_apply_csr_noalloc(cg_plan *p, const int32_t *row_ptr, co
                                           const float *vals, int64_t nnz, float *Y, void *stream) {
     using namespace cg;
     if (p == nullptr || Y == nullptr || row_ptr == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
-    if (nnz < 0 || nnz > 0x7fffffffLL) return CG_ERR_INVALID_ARG;
+    if (nnz < 0 || nnz > kMaxNnz) return CG_ERR_INVALID_ARG;
     if (nnz > 0 && (col_idx == nullptr || vals == nullptr)) return CG_ERR_INVALID_ARG;
     if (misaligned(row_ptr, 4) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
     if (p->precision != CG_PREC_FP32 || p->deterministic) return CG_ERR_UNSUPPORTED;

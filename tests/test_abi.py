@@ -105,6 +105,7 @@ def test_host_side_argument_errors_launch_nothing(lib):
     # negative nnz, nnz >= 2^31
     assert lib.cg_apply_csr(h, fake, fake, fake, -1, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_csr(h, fake, fake, fake, 1 << 31, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr(h, fake, fake, fake, (1 << 31) - (1 << 20) + 1, fake, fake, 1 << 30, P(0)) == 1
     # null outputs / inputs
     assert lib.cg_apply_csr(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_csr(h, P(0), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1
