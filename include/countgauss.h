@@ -145,7 +145,7 @@ typedef enum cg_op {
 /* ---- plans ---------------------------------------------------------------- */
 
 /* Create a plan for T = G.S with X of n rows and d columns, m output rows, B sketch
- * rows and the given seed (Section 1.1; Theorem 1).  Limits: 0 <= n < 2^31 - 1,
+ * rows and the given seed (Section 1.1; Theorem 1).  Limits: 0 <= n <= 2^31 - 2^20,
  * 1 <= d <= 65536, 1 <= m <= 65536, 1 <= B < 2^31, B.d < 2^40.  No CUDA call is made.
  * *out receives a host-side handle to free with cg_plan_destroy. */
 CG_API cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t seed, cg_plan **out);

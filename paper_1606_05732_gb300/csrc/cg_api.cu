@@ -201,7 +201,6 @@ using namespace cg;
 
 namespace {
 
-constexpr int64_t kMaxRows = (1LL << 31) - 2;
 constexpr int64_t kMaxB = (1LL << 31) - 1;
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }

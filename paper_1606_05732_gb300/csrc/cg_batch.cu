@@ -404,7 +404,7 @@ cg_status run(cg_batch_plan &P, void *ws, cudaStream_t st) {
 }
 
 bool valid_desc(const cg_batch_desc &D) {
-    if (D.n < 0 || D.n > (1LL << 31) - 2 || D.d < 1 || D.d > 65536 || D.m < 1 || D.m > 65536) return false;
+    if (D.n < 0 || D.n > kMaxRows || D.d < 1 || D.d > 65536 || D.m < 1 || D.m > 65536) return false;
     if (D.B < 1 || D.B > (1LL << 31) - 1 || D.B * static_cast<int64_t>(D.d) >= (1LL << 40)) return false;
     if (D.nnz < 0 || D.nnz > kMaxNnz || D.row_ptr == nullptr || D.Y == nullptr) return false;
     if (D.nnz > 0 && (D.col_idx == nullptr || D.vals == nullptr)) return false;

@@ -55,6 +55,8 @@ constexpr size_t kStatusBytes = 256;
 // nonzero indices never overflow when they step past the last entry (by at most a few
 // thousand per step).
 constexpr int64_t kMaxNnz = (1LL << 31) - (1LL << 20);
+// Most rows of X, with the same margin for the kernels' 32-bit row indices.
+constexpr int64_t kMaxRows = (1LL << 31) - (1LL << 20);
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 

@@ -62,7 +62,7 @@ def test_plan_validation(lib):
     assert st == 0 and h.value
     assert lib.cg_plan_destroy(h) == 0
     for bad in [(-1, 4, 8, 16), (10, 0, 8, 16), (10, 4, 0, 16), (10, 4, 8, 0), (10, 4, 8, 1 << 31),
-                (10, 70000, 8, 16)]:
+                (10, 70000, 8, 16), ((1 << 31) - (1 << 20) + 1, 4, 8, 16)]:
         st, h = _plan(lib, *bad)
         assert st == 1 and not h.value
 
