@@ -93,7 +93,11 @@ adjoint_w_kernel(const float *__restrict__ dY, int m, int d, int64_t B, Key key,
     }
 }
 
-// dX[i, :] = sigma(i) W[h(i), :] for dense dX (n x d, contiguous).
+// dX[i, :] = sigma(i) W[h(i), :] for dense dX (n x d, contiguous).  The vector path keeps
+// kGatherUnroll reads of W (L2-resident) in flight per lane before their stores, which
+// are streaming (dX is written once and not read back by this kernel).
+constexpr int kGatherUnroll = 4;
+
 __global__ void __launch_bounds__(kThreads)
 gather_dense_kernel(const float *__restrict__ W, int n, int d, uint32_t B, Key key, int64_t row_offset,
                     bool vec, float *__restrict__ dX) {
@@ -109,16 +113,25 @@ gather_dense_kernel(const float *__restrict__ W, int n, int d, uint32_t B, Key k
         if (vec) {
             const int dq = d >> 2;
             const int total = rows * dq;
-            for (int e0 = 0; e0 < total; e0 += 32) {
-                const int e = e0 + lane;
-                const int r = min(e / dq, 31);
-                const uint32_t hh = __shfl_sync(0xffffffffu, h, r);
-                const float s = __shfl_sync(0xffffffffu, sg, r);
-                if (e < total) {
-                    const int q = e - r * dq;
-                    const float4 x = __ldg(reinterpret_cast<const float4 *>(W + static_cast<size_t>(hh) * d) + q);
-                    reinterpret_cast<float4 *>(dX + static_cast<size_t>(first + r) * d)[q] =
-                        make_float4(s * x.x, s * x.y, s * x.z, s * x.w);
+            for (int e0 = 0; e0 < total; e0 += 32 * kGatherUnroll) {
+                float4 x[kGatherUnroll];
+                float s[kGatherUnroll];
+                int r[kGatherUnroll], q[kGatherUnroll];
+#pragma unroll
+                for (int u = 0; u < kGatherUnroll; ++u) {
+                    const int e = e0 + u * 32 + lane;
+                    r[u] = min(e / dq, 31);
+                    q[u] = e - r[u] * dq;
+                    const uint32_t hh = __shfl_sync(0xffffffffu, h, r[u]);
+                    s[u] = __shfl_sync(0xffffffffu, sg, r[u]);
+                    x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < total) x[u] = __ldg(reinterpret_cast<const float4 *>(W + static_cast<size_t>(hh) * d) + q[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kGatherUnroll; ++u) {
+                    if (e0 + u * 32 + lane < total)
+                        __stcs(reinterpret_cast<float4 *>(dX + static_cast<size_t>(first + r[u]) * d) + q[u],
+                               make_float4(s[u] * x[u].x, s[u] * x[u].y, s[u] * x[u].z, s[u] * x[u].w));
                 }
             }
         } else {

@@ -150,6 +150,32 @@ def test_deterministic_mode_is_bit_reproducible_and_exact(n, d, m, B, seed, kind
     assert rel(Y1, Yo) < FP32_TOL
 
 
+def test_deterministic_scale_sees_every_value_at_any_alignment():
+    """The fixed-point scale comes from max |x| over all stored values; the largest value
+    placed first, second, third, second-last or last, with the values starting at each
+    of the four 4-byte offsets within 16 bytes, gives the same bits (a missed maximum
+    would overflow the fixed-point sums) and the oracle's SX."""
+    n, d, m, B, seed = 5000, 16, 8, 256, 21
+    X = synth.csr_bernoulli(n, d, 0.1, seed=seed)
+    rp, ci, _ = dev_csr(X)
+    plan = cg().CountGauss(n, d, m, B, seed, deterministic=True)
+    for pos in (0, 1, 2, X.nnz - 2, X.nnz - 1):
+        vals = X.vals.copy()
+        vals[pos] = 3.0e5
+        ref = None
+        for off in range(4):
+            buf = torch.zeros(X.nnz + 4, dtype=torch.float32, device="cuda")
+            buf[off:off + X.nnz] = torch.from_numpy(vals).cuda()
+            SX = plan.sketch_csr(rp, ci, buf[off:off + X.nnz]).cpu().numpy()
+            if ref is None:
+                ref = SX
+            else:
+                np.testing.assert_array_equal(SX, ref)
+        plan.check()
+        SXo = oracle.sketch_csr(seed, n, d, B, X.row_ptr, X.col_idx, vals)
+        assert rel(ref, SXo) < 1e-6
+
+
 @pytest.mark.parametrize("rows", [1, 32, 64, 128])
 @pytest.mark.parametrize("passes", [1, 3])
 @pytest.mark.parametrize("n,d,m,B,seed,kind", [CASES[2], CASES[3], CASES[5], (70001, 128, 16, 5000, 17, "bern0.01")])
