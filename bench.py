@@ -42,8 +42,8 @@ UNIT = "nnz/s"
 
 # dram bytes (read + write) per launch of the scatter kernel from one ncu capture of the
 # workload named, keyed by the sha256 of the kernel source it was taken on (null once the
-# source changes).  nmf_n16M_d64: 537.02 MB read + 3.22 MB written, captured at full size.
-NCU_TRAFFIC = {("302269fad4ae6219", "nmf_n16M_d64"): 540_240_640}
+# source changes).  nmf_n16M_d64: 536.82 MB read + 3.23 MB written, captured at full size.
+NCU_TRAFFIC = {("ad38512167c92068", "nmf_n16M_d64"): 540_050_432}
 
 
 def parse_args():

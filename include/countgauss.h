@@ -113,6 +113,12 @@ typedef enum cg_option {
     CG_OPT_HOST_CHUNK = 10,   /* cg_apply_csr_host: most nonzeros, and most rows, per chunk copied
                                  to the device; 0 = automatic (nnz / 4 within [2^20, 2^24]), else
                                  32 .. 2^30 */
+    CG_OPT_ACCUMULATE = 12,   /* cg_sketch_csr / cg_sketch_dense: 0 (default) = SX is overwritten with
+                                 S.X; 1 = S.X is added into the caller's SX.  S.X is additive over
+                                 the rows of X, so a matrix fed in row chunks (each with its global
+                                 row offset, CG_OPT_ROW_OFFSET) sketches into one SX, and a saved SX
+                                 plus the next row offset resumes an interrupted stream.  Not with
+                                 CG_OPT_DETERMINISTIC or the partitioned scatter (CG_ERR_UNSUPPORTED) */
     CG_OPT_HOST_READ = 11     /* cg_apply_csr_host: how the kernels get the host CSR.  0 = automatic
                                  (copied), 1 = copied in chunks by the copy engine, 2 = direct: the
                                  scatter kernel reads the host arrays in place over the CPU-GPU
@@ -219,7 +225,7 @@ CG_API cg_status cg_plain_gaussian_apply(cg_plan *plan, const int32_t *row_ptr, 
 /* ---- stages (for stage-wise checks and measurement) ----------------------- */
 
 /* SX = S.X alone (Section 1.1: O(nnz(X)) scatter).  SX (device, B x d) is
- * overwritten.  Honours CG_OPT_DETERMINISTIC. */
+ * overwritten, or added into with CG_OPT_ACCUMULATE = 1.  Honours CG_OPT_DETERMINISTIC. */
 CG_API cg_status cg_sketch_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
                         const float *vals, int64_t nnz, float *SX,
                         void *ws, size_t ws_bytes, void *stream);

@@ -30,6 +30,7 @@ OP_APPLY_CSR_HOST = 7
 OP_APPLY_RIGHT_CSR = 8
 OPT_HOST_CHUNK = 10
 OPT_HOST_READ = 11
+OPT_ACCUMULATE = 12
 HOST_READ = {"auto": 0, "copied": 1, "direct": 2}
 
 P = ctypes.c_void_p

@@ -240,26 +240,43 @@ class CountGauss:
         return Z, imax, imin
 
     # -- stages -----------------------------------------------------------------
-    def sketch_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
+    def _sketch_out(self, out, accumulate: bool, dev) -> torch.Tensor:
+        if accumulate and out is None:
+            raise ValueError("accumulate=True needs out=SX to add into")
+        if out is not None and (out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != self.B * self.d):
+            raise ValueError(f"out must be a contiguous float32 tensor of B x d = {self.B} x {self.d}")
+        self.set_option(_lib.OPT_ACCUMULATE, int(bool(accumulate)))
+        return torch.empty(self.B, self.d, dtype=torch.float32, device=dev) if out is None else out
+
+    def sketch_csr(self, row_ptr, col_idx, vals, out=None, accumulate: bool = False) -> torch.Tensor:
+        """SX = S.X (Section 1.1), or SX += S.X into `out` with accumulate=True: rows of X fed
+        in chunks (each with its global row offset, set_row_offset) sketch into one SX, and a
+        saved SX plus the next row offset resumes the stream."""
         row_ptr = _need(row_ptr, torch.int32, "row_ptr")
         col_idx = _need(col_idx, torch.int32, "col_idx")
         vals = _need(vals, torch.float32, "vals")
         dev = row_ptr.device
         nnz = col_idx.numel()
-        SX = torch.empty(self.B, self.d, dtype=torch.float32, device=dev) if out is None else out
+        SX = self._sketch_out(out, accumulate, dev)
         ws = self.workspace(_lib.OP_SKETCH, nnz, dev)
         _lib.check("cg_sketch_csr", self._lib.cg_sketch_csr(
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(SX), _ptr(ws), ws.numel(), _stream(dev)))
         return SX
 
-    def sketch_dense(self, X, out=None) -> torch.Tensor:
+    def sketch_dense(self, X, out=None, accumulate: bool = False) -> torch.Tensor:
+        """SX = S.X for dense X, or SX += S.X into `out` with accumulate=True."""
         X = _need(X, torch.float32, "X")
         dev = X.device
-        SX = torch.empty(self.B, self.d, dtype=torch.float32, device=dev) if out is None else out
+        SX = self._sketch_out(out, accumulate, dev)
         ws = self.workspace(_lib.OP_SKETCH, 0, dev)
         _lib.check("cg_sketch_dense", self._lib.cg_sketch_dense(
             self._h, _ptr(X), X.shape[1], _ptr(SX), _ptr(ws), ws.numel(), _stream(dev)))
         return SX
+
+    def set_row_offset(self, row_offset: int) -> None:
+        """Global index of local row 0 (CG_OPT_ROW_OFFSET), e.g. per chunk of a stream."""
+        self.set_option(_lib.OPT_ROW_OFFSET, int(row_offset))
+        self.row_offset = int(row_offset)
 
     def contract(self, SX, out=None) -> torch.Tensor:
         SX = _need(SX, torch.float32, "SX")

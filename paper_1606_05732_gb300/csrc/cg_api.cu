@@ -354,8 +354,9 @@ cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const La
                                           timing_pair(p, CG_KERNEL_CONTRACT), st, transpose));
 }
 
+// SX = S.X, or with clear = false SX += S.X (atomic and deferred scatters only).
 cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
-                         int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st) {
+                         int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st, bool clear = true) {
     if (p->deterministic)
         return from_cuda(launch_sketch_csr_fixed(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                                  static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
@@ -367,7 +368,7 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
                                                     static_cast<uint32_t>(p->B), static_cast<int>(nnz),
                                                     make_key(p->seed), p->row_offset, SX, status_word(ws),
                                                     region(ws, L.c_off), static_cast<int>(p->sketch_ctas),
-                                                    p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st));
+                                                    p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st, clear));
     if (use_partition(*p))
         return from_cuda(launch_sketch_csr_partitioned(
             row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), static_cast<int>(nnz),
@@ -376,7 +377,8 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
     return from_cuda(launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                               static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
                                               p->row_offset, SX, status_word(ws), static_cast<int>(p->sketch_ctas),
-                                              p->scatter_passes, p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st));
+                                              p->scatter_passes, p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st,
+                                              clear));
 }
 
 // Device address of the page-locked host range [p, p + bytes), or nullptr when the
@@ -503,6 +505,7 @@ cg_status cg_plan_create(int64_t n, int32_t d, int32_t m, int64_t B, uint64_t se
     p->scatter_rows = 0;
     p->host_chunk = 0;
     p->host_read = 0;
+    p->accumulate = 0;
     p->host_state = nullptr;
     *out = p;
     return CG_OK;
@@ -588,6 +591,10 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             if (value < 0 || value > 2) return CG_ERR_INVALID_ARG;
             p->host_read = static_cast<int32_t>(value);
             return CG_OK;
+        case CG_OPT_ACCUMULATE:
+            if (value != 0 && value != 1) return CG_ERR_INVALID_ARG;
+            p->accumulate = static_cast<int32_t>(value);
+            return CG_OK;
         default:
             return CG_ERR_INVALID_ARG;
     }
@@ -607,6 +614,7 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
         case CG_OPT_SCATTER_ROWS: *value = p->scatter_rows; return CG_OK;
         case CG_OPT_HOST_CHUNK: *value = p->host_chunk; return CG_OK;
         case CG_OPT_HOST_READ: *value = p->host_read; return CG_OK;
+        case CG_OPT_ACCUMULATE: *value = p->accumulate; return CG_OK;
         default: return CG_ERR_INVALID_ARG;
     }
 }
@@ -639,7 +647,8 @@ cg_status cg_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_i
     if (s != CG_OK) return s;
     Layout L;
     if ((s = check_ws(p, CG_OP_SKETCH, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
-    return run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, L, as_stream(stream));
+    if (p->accumulate && (p->deterministic || use_partition(*p))) return CG_ERR_UNSUPPORTED;
+    return run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, L, as_stream(stream), !p->accumulate);
 }
 
 cg_status cg_sketch_dense(cg_plan *p, const float *X, int64_t ldx, float *SX, void *ws, size_t ws_bytes,
@@ -653,7 +662,7 @@ cg_status cg_sketch_dense(cg_plan *p, const float *X, int64_t ldx, float *SX, vo
     return from_cuda(launch_sketch_dense_atomic(X, ldx, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
                                                 make_key(p->seed), p->row_offset, SX, status_word(ws),
                                                 static_cast<int>(p->sketch_ctas), timing_pair(p, CG_KERNEL_SKETCH),
-                                                as_stream(stream)));
+                                                as_stream(stream), !p->accumulate));
 }
 
 cg_status cg_contract(cg_plan *p, const float *SX, float *Y, void *ws, size_t ws_bytes, void *stream) {

@@ -26,6 +26,7 @@ struct cg_plan {
     int32_t scatter_rows;   // CG_OPT_SCATTER_ROWS (0 = auto)
     int64_t host_chunk;     // CG_OPT_HOST_CHUNK (0 = auto)
     int32_t host_read;      // CG_OPT_HOST_READ (0 = auto, 1 = copied, 2 = direct)
+    int32_t accumulate;     // CG_OPT_ACCUMULATE (cg_sketch_*: 1 = add into SX)
     void *host_state;       // copy stream and events of cg_apply_csr_host, created on first use
 };
 
@@ -70,12 +71,14 @@ int num_sms();
 int resident_ctas_per_sm(const void *kernel, int threads, size_t dyn_smem, int tmem_cols);
 
 // ---- scatter (cg_sketch.cu) -------------------------------------------------
+// The scatter launchers clear SX first unless `clear` is false (then they add into it).
 cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream);
+                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream,
+                                     bool clear = true);
 cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d, uint32_t B, Key key,
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
-                                       cudaStream_t stream);
+                                       cudaStream_t stream, bool clear = true);
 int sketch_default_ctas();
 // Rows [0, n) of a chunk of a CSR matrix into SX (no clearing, one pass): row_ptr holds
 // the chunk's n + 1 offsets into the whole matrix, col_idx / vals hold its nonzeros
@@ -98,7 +101,8 @@ int sketch_deferred_ctas(int ctas);
 size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas);
 cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                        uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream);
+                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
+                                       bool clear = true);
 
 // Bytes of the L2 of the current device (cached per device; 0 without a device).
 int l2_bytes();

@@ -208,8 +208,9 @@ int sketch_default_ctas() {
 
 cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream) {
-    cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
+                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream,
+                                     bool clear) {
+    cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
     if (e != cudaSuccess || n == 0) return e;
     rows = chunk_rows(n, nnz, rows);
     const int nchunks = (n + chunk_height(rows) - 1) / chunk_height(rows);
@@ -278,9 +279,9 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
 
 cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d, uint32_t B, Key key,
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
-                                       cudaStream_t stream) {
+                                       cudaStream_t stream, bool clear) {
     (void)status;
-    cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
+    cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
     if (e != cudaSuccess || n == 0) return e;
     const int nchunks = (n + 31) / 32;
     const int need = (nchunks + kWarps - 1) / kWarps;

@@ -237,8 +237,9 @@ int sketch_deferred_ctas(int ctas) { return ctas > 0 ? ctas : sketch_default_cta
 
 cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                        uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream) {
-    cudaError_t e = cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream);
+                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
+                                       bool clear) {
+    cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
     if (e != cudaSuccess || n == 0) return e;
     const int G = sketch_deferred_ctas(ctas);
     const int H = staged_rows(n, nnz, rows);

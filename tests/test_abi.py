@@ -77,7 +77,7 @@ def test_options_and_workspace(lib):
     assert lib.cg_plan_set_option(h, 3, 12345) == 0
     assert lib.cg_plan_get_option(h, 3, ctypes.byref(val)) == 0 and val.value == 12345
     for opt, good, bad in [(8, (0, 1, 16), (-1, 17)), (9, (0, 1, 32, 64, 128), (2, 16, 33, 256, -32)),
-                           (11, (0, 1, 2), (-1, 3))]:
+                           (11, (0, 1, 2), (-1, 3)), (12, (0, 1), (-1, 2))]:
         for x in good:
             assert lib.cg_plan_set_option(h, opt, x) == 0
             assert lib.cg_plan_get_option(h, opt, ctypes.byref(val)) == 0 and val.value == x
@@ -119,6 +119,9 @@ def test_host_side_argument_errors_launch_nothing(lib):
     assert lib.cg_apply_right_csr(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
     assert lib.cg_plan_set_option(h, 2, 1) == 0
     assert lib.cg_apply_right_csr(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
+    # accumulating into SX is not offered with the deterministic (fixed-point) scatter
+    assert lib.cg_plan_set_option(h, 12, 1) == 0
+    assert lib.cg_sketch_csr(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
     lib.cg_plan_destroy(h)
 
 
