@@ -642,6 +642,7 @@ cg_status cg_plan_check(const cg_plan *p, void *ws, void *stream) {
 
 cg_status cg_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals, int64_t nnz,
                         float *SX, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_sketch_csr");
     if (p == nullptr || SX == nullptr || misaligned(SX, 16)) return CG_ERR_INVALID_ARG;
     cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
     if (s != CG_OK) return s;
@@ -653,6 +654,7 @@ cg_status cg_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_i
 
 cg_status cg_sketch_dense(cg_plan *p, const float *X, int64_t ldx, float *SX, void *ws, size_t ws_bytes,
                           void *stream) {
+    cg::NvtxRange nvtx_range("cg_sketch_dense");
     if (p == nullptr || SX == nullptr || misaligned(SX, 16) || ldx < p->d) return CG_ERR_INVALID_ARG;
     if (p->n > 0 && (X == nullptr || misaligned(X, 4))) return CG_ERR_INVALID_ARG;
     cg_status s;
@@ -666,6 +668,7 @@ cg_status cg_sketch_dense(cg_plan *p, const float *X, int64_t ldx, float *SX, vo
 }
 
 cg_status cg_contract(cg_plan *p, const float *SX, float *Y, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_contract");
     if (p == nullptr || SX == nullptr || Y == nullptr || misaligned(SX, 4) || misaligned(Y, 4))
         return CG_ERR_INVALID_ARG;
     cg_status s;
@@ -676,6 +679,7 @@ cg_status cg_contract(cg_plan *p, const float *SX, float *Y, void *ws, size_t ws
 
 cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals, int64_t nnz,
                        float *Y, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_csr");
     if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
     cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
     if (s != CG_OK) return s;
@@ -689,6 +693,7 @@ cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_id
 
 cg_status cg_apply_right_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                              int64_t nnz, float *Z, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_right_csr");
     if (p == nullptr || Z == nullptr || misaligned(Z, 4)) return CG_ERR_INVALID_ARG;
     cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
     if (s != CG_OK) return s;
@@ -706,6 +711,7 @@ cg_status cg_apply_right_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *
 
 cg_status cg_apply_dense(cg_plan *p, const float *X, int64_t ldx, float *Y, void *ws, size_t ws_bytes,
                          void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_dense");
     if (p == nullptr || Y == nullptr || misaligned(Y, 4) || ldx < p->d) return CG_ERR_INVALID_ARG;
     if (p->n > 0 && (X == nullptr || misaligned(X, 4))) return CG_ERR_INVALID_ARG;
     cg_status s;
@@ -723,6 +729,7 @@ cg_status cg_apply_dense(cg_plan *p, const float *X, int64_t ldx, float *Y, void
 
 cg_status cg_apply_adjoint(cg_plan *p, const float *dY, const int32_t *row_ptr, const int32_t *col_idx, int64_t nnz,
                            float *dX, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_adjoint");
     if (p == nullptr || dY == nullptr || misaligned(dY, 4) || misaligned(dX, 4)) return CG_ERR_INVALID_ARG;
     const bool sparse = row_ptr != nullptr;
     cg_status s;
@@ -746,6 +753,7 @@ cg_status cg_apply_adjoint(cg_plan *p, const float *dY, const int32_t *row_ptr, 
 
 cg_status cg_plain_gaussian_apply(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                                   int64_t nnz, float *Y, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_plain_gaussian_apply");
     if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
     cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
     if (s != CG_OK) return s;
@@ -784,6 +792,7 @@ cg_status cg_generate_gaussian(uint64_t seed, uint32_t tag, int64_t R, int64_t r
 
 cg_status cg_apply_csr_host(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                             int64_t nnz, float *Y, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_csr_host");
     if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
     cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
     if (s != CG_OK) return s;
@@ -865,6 +874,7 @@ cg_status cg_apply_csr_host(cg_plan *p, const int32_t *row_ptr, const int32_t *c
 }
 
 cg_status cg_diag_random_reductions(float *array, int64_t cells, int64_t count, void *stream) {
+    cg::NvtxRange nvtx_range("cg_diag_random_reductions");
     if (array == nullptr || misaligned(array, 4) || cells < 1 || cells >= (1LL << 32) || count < 0 ||
         count >= (1LL << 32))
         return CG_ERR_INVALID_ARG;

@@ -493,6 +493,7 @@ cg_status cg_batch_workspace_size(const cg_batch_plan *P, size_t *bytes) {
 }
 
 cg_status cg_batch_apply(cg_batch_plan *P, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_batch_apply");
     if (P == nullptr || ws == nullptr || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return CG_ERR_INVALID_ARG;
     if (ws_bytes < P->total) return CG_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -519,6 +520,7 @@ cg_status cg_batch_check(const cg_batch_plan *P, void *ws, void *stream) {
 }
 
 cg_status cg_batch_autotune(cg_batch_plan *P, void *ws, size_t ws_bytes, void *stream, int32_t reps, double *best_ms) {
+    cg::NvtxRange nvtx_range("cg_batch_autotune");
     if (P == nullptr || ws == nullptr || reps < 1 || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
         return CG_ERR_INVALID_ARG;
     if (ws_bytes < P->total) return CG_ERR_WORKSPACE;

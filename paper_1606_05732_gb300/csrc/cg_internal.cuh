@@ -1,6 +1,7 @@
 // cg_internal.cuh -- declarations shared by the translation units of libcountgauss.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -31,6 +32,16 @@ struct cg_plan {
 };
 
 namespace cg {
+
+// An NVTX range named after a C-ABI call, open for the call's duration (profiler
+// timelines show which call enqueued which kernels; without a tool attached it is a no-op).
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // A pair of events recorded immediately before and after one kernel launch.
 struct EventPair {

@@ -56,6 +56,7 @@ row_argmax_argmin_kernel(const float *__restrict__ Z, int m, int d, int32_t *__r
 
 extern "C" cg_status cg_row_argmax_argmin(const float *Z, int32_t m, int32_t d, int32_t *imax, int32_t *imin,
                                           void *stream) {
+    cg::NvtxRange nvtx_range("cg_row_argmax_argmin");
     using namespace cg;
     if (m < 0 || d < 1 || (m > 0 && (Z == nullptr || imax == nullptr || imin == nullptr))) return CG_ERR_INVALID_ARG;
     if (m == 0) return CG_OK;
@@ -66,6 +67,7 @@ extern "C" cg_status cg_row_argmax_argmin(const float *Z, int32_t m, int32_t d, 
 extern "C" cg_status cg_nmf_anchors_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
                                         const float *vals, int64_t nnz, float *Z, int32_t *imax, int32_t *imin,
                                         void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_nmf_anchors_csr");
     if (plan == nullptr) return CG_ERR_INVALID_ARG;
     const cg_status s = cg_apply_csr(plan, row_ptr, col_idx, vals, nnz, Z, ws, ws_bytes, stream);
     if (s != CG_OK) return s;

@@ -53,6 +53,7 @@ bool misaligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t
 
 extern "C" cg_status cg_apply_csr_noalloc(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx,
                                           const float *vals, int64_t nnz, float *Y, void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_csr_noalloc");
     using namespace cg;
     if (p == nullptr || Y == nullptr || row_ptr == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
     if (nnz < 0 || nnz > kMaxNnz) return CG_ERR_INVALID_ARG;

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) sumsq_f64_kernel(const float *__restrict_
 
 extern "C" cg_status cg_moments_f64(const float *Y, int64_t rows, int32_t d, double *gram, double *sumsq,
                                     void *stream) {
+    cg::NvtxRange nvtx_range("cg_moments_f64");
     using namespace cg;
     if (rows < 0 || d < 1 || d > 65536 || (rows > 0 && Y == nullptr)) return CG_ERR_INVALID_ARG;
     if (gram == nullptr && sumsq == nullptr) return CG_ERR_INVALID_ARG;
