@@ -94,3 +94,30 @@ def test_fullsize_batch_96_instances():
         worst = max(worst, rel(Y, Yo))
     print(f"batch of 96: worst rel Frobenius error {worst:.3e}")
     assert worst < FP32_TOL
+
+
+def test_fullsize_grad_dense_forward_and_adjoints():
+    """The differentiation workload at its benchmark size: dense X 2^20 x 64, m = 64,
+    B = 2^16 (forward through the dense sketch, adjoint as a dense gather), and the
+    adjoint read at the 1.34 M stored entries of the p = 0.02 pattern, all against the
+    oracle in full."""
+    from paper_1606_05732_gb300 import countgauss
+    w = synth.WORKLOADS["grad_n1M_d64"]
+    n, d, m, B, seed = w["n"], w["d"], w["m"], w["B"], w["seed"]
+    Xd = synth.dense_normal(n, d, seed=seed)
+    Xs = synth.csr_bernoulli(n, d, w["p"], seed=seed)
+    dY = np.random.default_rng(seed + 1).standard_normal((m, d)).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    plan = countgauss.CountGauss(n, d, m, B, seed)
+    Y = plan.apply_dense(torch.from_numpy(Xd).to(dev)).cpu().numpy()
+    dX = plan.adjoint(torch.from_numpy(dY).to(dev)).cpu().numpy()
+    rp = torch.from_numpy(Xs.row_ptr.astype(np.int32)).to(dev)
+    ci = torch.from_numpy(Xs.col_idx).to(dev)
+    dXs = plan.adjoint(torch.from_numpy(dY).to(dev), rp, ci).cpu().numpy()
+    plan.check()
+    err_f = rel(Y, oracle.apply_dense(seed, m, B, Xd.astype(np.float64)))
+    dY64 = dY.astype(np.float64)
+    err_d = rel(dX, oracle.adjoint_dense(seed, n, m, B, dY64))
+    err_s = rel(dXs, oracle.adjoint_csr(seed, n, m, B, Xs.row_ptr, Xs.col_idx, dY64))
+    print(f"grad_n1M_d64: forward {err_f:.3e}, dense adjoint {err_d:.3e}, CSR adjoint {err_s:.3e}")
+    assert err_f < FP32_TOL and err_d < FP32_TOL and err_s < FP32_TOL
