@@ -413,13 +413,14 @@ def test_diag_random_reductions_adds_exactly_count():
         cg().diag_random_reductions(a, -1)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("n,d,m,B,seed", [(64, 65536, 4, 8, 51), (1000, 4, 65536, 16, 52)])
-def test_largest_d_and_m(n, d, m, B, seed):
-    """The widest X (d = 65536 columns, 512 column tiles of the contraction) and the
-    tallest output (m = 65536 rows of G, 1024 row tiles), each at the plan's limit."""
+def test_largest_d_and_m(n, d, m, B, seed, precision):
+    """The widest X (d = 65536 columns: 512 FFMA column tiles, 256 tensor-core ones) and
+    the tallest output (m = 65536 rows of G), each at the plan's limit."""
     X = synth.csr_bernoulli(n, d, 0.01 if d > 1000 else 0.5, seed=seed)
     rp, ci, v = dev_csr(X)
-    plan = cg().CountGauss(n, d, m, B, seed)
+    plan = cg().CountGauss(n, d, m, B, seed, precision=precision)
     Y = plan.apply_csr(rp, ci, v).cpu().numpy()
     plan.check()
     Yo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals)
