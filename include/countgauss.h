@@ -68,7 +68,7 @@ typedef struct cg_plan cg_plan;
 typedef enum cg_status {
     CG_OK = 0,
     CG_ERR_INVALID_ARG = 1,   /* bad size, null pointer, misaligned buffer */
-    CG_ERR_UNSUPPORTED = 2,   /* valid request outside what this build implements */
+    CG_ERR_UNSUPPORTED = 2,   /* valid request outside what the library implements */
     CG_ERR_WORKSPACE = 3,     /* ws_bytes smaller than cg_workspace_size() */
     CG_ERR_CUDA = 4,          /* a CUDA call or kernel launch failed */
     CG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (batched path) */

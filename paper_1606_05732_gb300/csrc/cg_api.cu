@@ -470,7 +470,7 @@ const char *cg_status_string(cg_status s) {
     switch (s) {
         case CG_OK: return "CG_OK";
         case CG_ERR_INVALID_ARG: return "CG_ERR_INVALID_ARG: invalid argument";
-        case CG_ERR_UNSUPPORTED: return "CG_ERR_UNSUPPORTED: request not supported by this build";
+        case CG_ERR_UNSUPPORTED: return "CG_ERR_UNSUPPORTED: request not supported by the library";
         case CG_ERR_WORKSPACE: return "CG_ERR_WORKSPACE: workspace too small";
         case CG_ERR_CUDA: return "CG_ERR_CUDA: a CUDA call or kernel launch failed";
         case CG_ERR_TIMEOUT: return "CG_ERR_TIMEOUT: a bounded device wait gave up";
