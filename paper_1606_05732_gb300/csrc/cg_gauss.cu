@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(kThreads)
 contract_ffma_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_split,
                      bool vec_x, float *__restrict__ part) {
     __shared__ __align__(16) float raw[FfmaShape<TN>::kRawFloats];
+    pdl_wait();  // SX comes from the scatter launched before
     const int64_t nslabs = (B + kKT - 1) / kKT;
     const int64_t s_begin = static_cast<int64_t>(blockIdx.x) * slabs_per_split;
     const int64_t s_end = min(nslabs, s_begin + slabs_per_split);
@@ -50,6 +51,7 @@ constexpr int red_threads() { return W >= 8 ? W * 32 : 256; }
 template <int W>
 __global__ void __launch_bounds__(red_threads<W>())
 reduce_splits_kernel(const float *__restrict__ part, int nsplit, int64_t total, int tr_cols, float *__restrict__ Y) {
+    pdl_wait();  // the partials come from the kernel launched before
     constexpr int kGroups = red_threads<W>() / (32 * W);
     __shared__ float red[W > 1 ? red_threads<W>() / 32 : 1][33];
     const int lane = threadIdx.x & 31;
@@ -95,9 +97,9 @@ cudaError_t launch_reduce_w(const float *partials, int nsplit, int64_t total, fl
     constexpr int kGroups = red_threads<W>() / (32 * W);
     const int64_t groups = (total + 31) / 32;
     const int64_t grid = (groups + kGroups - 1) / kGroups;
-    reduce_splits_kernel<W><<<static_cast<unsigned>(grid), red_threads<W>(), 0, stream>>>(partials, nsplit, total,
-                                                                                          tr_cols, Y);
-    return cudaGetLastError();
+    const cudaError_t e = launch_after_previous(reduce_splits_kernel<W>, dim3(static_cast<unsigned>(grid)),
+                                                dim3(red_threads<W>()), 0, stream, partials, nsplit, total, tr_cols, Y);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -149,15 +151,18 @@ cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key k
     const int gm = (m + kBM - 1) / kBM;
     const bool vec_x = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(SX) & 15) == 0);
     record(ev, true, stream);
+    cudaError_t e;
     if (d > 64) {
         const int gn = (d + 127) / 128;
-        contract_ffma_kernel<8><<<dim3(used, gm, gn), kThreads, 0, stream>>>(SX, m, d, B, key, per, vec_x, partials);
+        e = launch_after_previous(contract_ffma_kernel<8>, dim3(used, gm, gn), dim3(kThreads), 0, stream, SX, m, d, B, key,
+                                  per, vec_x, partials);
     } else {
         const int gn = (d + 63) / 64;
-        contract_ffma_kernel<4><<<dim3(used, gm, gn), kThreads, 0, stream>>>(SX, m, d, B, key, per, vec_x, partials);
+        e = launch_after_previous(contract_ffma_kernel<4>, dim3(used, gm, gn), dim3(kThreads), 0, stream, SX, m, d, B, key,
+                                  per, vec_x, partials);
     }
     record(ev, false, stream);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream, transpose ? d : 0);
 }

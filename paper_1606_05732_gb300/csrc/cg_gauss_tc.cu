@@ -85,6 +85,7 @@ template <int NT, bool SPLIT3>
 __global__ void __launch_bounds__(bf16_threads<NT, SPLIT3>(), 1)
 contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_cta,
                         float *__restrict__ part, int *__restrict__ status) {
+    pdl_wait();  // SX comes from the scatter launched before
     using C = Cfg<NT, SPLIT3>;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -263,10 +264,10 @@ cudaError_t launch_tc(const float *SX, int m, int d, int64_t B, Key key, int nsp
     if (e != cudaSuccess) return e;
     dim3 grid(used, (d + NT - 1) / NT, (m + kM - 1) / kM);
     record(ev, true, stream);
-    contract_tc_bf16_kernel<NT, SPLIT3><<<grid, bf16_threads<NT, SPLIT3>(), smem, stream>>>(SX, m, d, B, key, per,
-                                                                                      partials, status);
+    e = launch_after_previous(contract_tc_bf16_kernel<NT, SPLIT3>, grid, dim3(bf16_threads<NT, SPLIT3>()), smem, stream,
+                              SX, m, d, B, key, per, partials, status);
     record(ev, false, stream);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int tc_nt(int d) { return d <= 64 ? 64 : (d <= 128 ? 128 : 256); }
@@ -309,6 +310,7 @@ template <int NT, bool SPLIT3>
 __global__ void __launch_bounds__(kThreads, 1)
 contract_tc_fp8_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_cta,
                        float *__restrict__ part, int *__restrict__ status) {
+    pdl_wait();  // SX comes from the scatter launched before
     using C = Cfg8<NT, SPLIT3>;
     extern __shared__ uint8_t dsmem[];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -522,9 +524,10 @@ cudaError_t launch_tc8(const float *SX, int m, int d, int64_t B, Key key, int ns
     if (e != cudaSuccess) return e;
     dim3 grid(used, (d + NT - 1) / NT, (m + kM - 1) / kM);
     record(ev, true, stream);
-    contract_tc_fp8_kernel<NT, SPLIT3><<<grid, kThreads, smem, stream>>>(SX, m, d, B, key, per, partials, status);
+    e = launch_after_previous(contract_tc_fp8_kernel<NT, SPLIT3>, grid, dim3(kThreads), smem, stream, SX, m, d, B, key,
+                              per, partials, status);
     record(ev, false, stream);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int tc8_nt(int d) { return d <= 64 ? 64 : 128; }

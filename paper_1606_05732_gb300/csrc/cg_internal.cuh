@@ -57,6 +57,28 @@ inline void record(const EventPair *ev, bool start, cudaStream_t s) {
     if (ev != nullptr) cudaEventRecord(start ? ev->start : ev->stop, s);
 }
 
+// Programmatic dependent launch: a kernel launched with launch_after_previous may be
+// scheduled while the kernel before it in the stream is finishing (its blocks exit), and
+// must call pdl_wait() before it reads anything that kernel wrote.  pdl_wait() returns at
+// once for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_after_previous(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                                  Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Device status word bits (first word of every workspace).
 constexpr int kStatusBounds = 1;
 constexpr int kStatusTimeout = 2;
