@@ -107,9 +107,11 @@ typedef enum cg_option {
                                  that range of SX in L2); 0 = automatic (one pass), 1..16 forced */
     CG_OPT_SCATTER_ROWS = 9,  /* CSR rows per warp chunk of the scatter: 0 = automatic (the
                                  smallest of 32, 64, 128 whose chunk holds about 96 nonzeros on
-                                 average), 32, 64, 128 forced (rows staged in shared memory,
-                                 nonzeros swept 32 at a time), or 1 (one row per lane, each
-                                 lane walking its own row) */
+                                 average; 256 in the deferred scatter for rows of under 1.5
+                                 nonzeros), 32, 64, 128 forced (rows staged in shared memory,
+                                 nonzeros swept 32 at a time), 256 forced (deferred scatter only;
+                                 the others take it as automatic), or 1 (one row per lane, each
+                                 lane walking its own row; one-pass scatters only) */
     CG_OPT_HOST_CHUNK = 10,   /* cg_apply_csr_host: most nonzeros, and most rows, per chunk copied
                                  to the device; 0 = automatic (nnz / 4 within [2^20, 2^24]), else
                                  32 .. 2^30 */

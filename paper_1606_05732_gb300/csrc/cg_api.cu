@@ -580,7 +580,8 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             p->scatter_passes = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_SCATTER_ROWS:
-            if (value != 0 && value != 1 && value != 32 && value != 64 && value != 128) return CG_ERR_INVALID_ARG;
+            if (value != 0 && value != 1 && value != 32 && value != 64 && value != 128 && value != 256)
+                return CG_ERR_INVALID_ARG;
             p->scatter_rows = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_HOST_CHUNK:

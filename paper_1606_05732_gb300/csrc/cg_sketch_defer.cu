@@ -45,7 +45,7 @@ template <int ROWS>
 __device__ __forceinline__ bool stage_chunk(const int *__restrict__ row_ptr, int first, int n, int nnz, uint32_t B,
                                             Key key, int64_t row_offset, int *s_rp, uint32_t *s_h, float *s_sg,
                                             uint64_t pol, int &beg, int &end, int &bad) {
-    static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128, "chunk height");
+    static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128 || ROWS == 256, "chunk height");
     constexpr int R = ROWS / 32;
     const int lane = threadIdx.x & 31;
     const int last = min(first + ROWS, n);
@@ -217,12 +217,16 @@ replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, 
     }
 }
 
+// Chunk height of pass 1: as for the one-pass scatter (about 96 nonzeros per chunk), but
+// 256 rows for rows of under 1.5 nonzeros: eight independent hashes per lane and fewer
+// chunk boundaries (at 1.28 nonzeros per row, 0.976 ms against 1.010 ms with 128 rows).
 int staged_rows(int n, int nnz, int forced) {
-    if (forced == 32 || forced == 64 || forced == 128) return forced;
+    if (forced == 32 || forced == 64 || forced == 128 || forced == 256) return forced;
     const double per_row = n > 0 ? static_cast<double>(nnz) / n : 0.0;
     if (per_row * 32 >= 96.0) return 32;
     if (per_row * 64 >= 96.0) return 64;
-    return 128;
+    if (per_row >= 1.5) return 128;
+    return 256;
 }
 
 }  // namespace
@@ -251,6 +255,10 @@ cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, c
     const uint32_t bsplit = B / 2;
     record(ev, true, stream);
     switch (H) {
+        case 256:
+            split_pass_kernel<256><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                                  SX, bsplit, rows_per_cta, records, counts, status);
+            break;
         case 128:
             split_pass_kernel<128><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
                                                                   SX, bsplit, rows_per_cta, records, counts, status);

@@ -76,7 +76,7 @@ def test_options_and_workspace(lib):
     assert lib.cg_plan_set_option(h, 99, 0) == 1
     assert lib.cg_plan_set_option(h, 3, 12345) == 0
     assert lib.cg_plan_get_option(h, 3, ctypes.byref(val)) == 0 and val.value == 12345
-    for opt, good, bad in [(8, (0, 1, 16), (-1, 17)), (9, (0, 1, 32, 64, 128), (2, 16, 33, 256, -32)),
+    for opt, good, bad in [(8, (0, 1, 16), (-1, 17)), (9, (0, 1, 32, 64, 128, 256), (2, 16, 33, 512, -32)),
                            (11, (0, 1, 2), (-1, 3)), (12, (0, 1), (-1, 2))]:
         for x in good:
             assert lib.cg_plan_set_option(h, opt, x) == 0

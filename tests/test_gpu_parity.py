@@ -198,7 +198,7 @@ def test_scatter_chunk_rows_and_passes(n, d, m, B, seed, kind, rows, passes):
     assert rel(SXd, SXo) < 1e-6
 
 
-@pytest.mark.parametrize("rows", [32, 64, 128])
+@pytest.mark.parametrize("rows", [32, 64, 128, 256])
 def test_deferred_scatter_edges(rows):
     """The deferred scatter (rows of the upper half of the buckets written as records,
     reduced by a second pass): CTA row ranges with ragged ends and empty rows, a row
