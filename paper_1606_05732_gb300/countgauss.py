@@ -56,7 +56,13 @@ def _need(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
 
 
 class CountGauss:
-    """A CountGauss plan T = G.S for X of n rows and d columns (cg_plan_create)."""
+    """A CountGauss plan T = G.S for X of n rows and d columns (cg_plan_create).
+
+    Calls run asynchronously on the current CUDA stream.  The calls made through one plan
+    share its device workspace (one per device, grown on demand), so issue them on one
+    stream, or synchronise between streams; use one plan per concurrent stream otherwise.
+    Plans are host objects of a few bytes, and plans with the same seed, m and B apply the
+    same T."""
 
     def __init__(self, n: int, d: int, m: int, B: int, seed: int, *, precision: str = "fp32",
                  deterministic: bool = False, row_offset: int = 0, ksplit: int = 0, sketch_ctas: int = 0,
