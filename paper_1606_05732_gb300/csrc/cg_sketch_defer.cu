@@ -189,10 +189,26 @@ split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
 }
 
-// Pass 2: CTA c reduces the counts[c] records of its region into SX.
+// Pass 2: CTA c reduces the counts[c] records of its region into SX.  First each CTA asks
+// for its share of the upper half of SX (cells [lo_cell, cells)) to be brought into L2,
+// where pass 1 left the lower half (a small gain: at the ladder size the pass is bound by
+// the issue of its random reductions, not by their L2 misses).
 __global__ void __launch_bounds__(kThreads)
 replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, const uint2 *__restrict__ records,
-                      const int *__restrict__ counts, uint32_t cells, float *__restrict__ SX) {
+                      const int *__restrict__ counts, uint32_t lo_cell, uint32_t cells, float *__restrict__ SX) {
+    if (threadIdx.x == 0 && cells > lo_cell) {
+        const uint64_t share = (static_cast<uint64_t>(cells - lo_cell) + gridDim.x - 1) / gridDim.x;
+        const uint64_t c0 = lo_cell + share * blockIdx.x;
+        const uint64_t c1 = c0 + share < cells ? c0 + share : cells;
+        if (c0 < c1) {
+            const uintptr_t a = (reinterpret_cast<uintptr_t>(SX + c0) + 15) & ~static_cast<uintptr_t>(15);
+            const uintptr_t e = reinterpret_cast<uintptr_t>(SX + c1) & ~static_cast<uintptr_t>(15);
+            for (uintptr_t q = a; q < e; q += (1u << 20)) {  // at most 1 MB per hint
+                const uint32_t len = static_cast<uint32_t>(e - q < (1u << 20) ? e - q : (1u << 20));
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(q), "r"(len) : "memory");
+            }
+        }
+    }
     const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
     const int r1 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(r0) + rows_per_cta));
     const int start = __ldg(row_ptr + r0);
@@ -273,6 +289,7 @@ cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, c
             break;
     }
     replay_records_kernel<<<used, kThreads, 0, stream>>>(row_ptr, n, rows_per_cta, records, counts,
+                                                         bsplit * static_cast<uint32_t>(d),
                                                          B * static_cast<uint32_t>(d), SX);
     record(ev, false, stream);
     return cudaGetLastError();
