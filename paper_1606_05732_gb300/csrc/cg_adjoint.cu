@@ -101,6 +101,7 @@ constexpr int kGatherUnroll = 4;
 __global__ void __launch_bounds__(kThreads)
 gather_dense_kernel(const float *__restrict__ W, int n, int d, uint32_t B, Key key, int64_t row_offset,
                     bool vec, float *__restrict__ dX) {
+    pdl_wait();  // W comes from the kernel launched before
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int nchunks = (n + 31) >> 5;
@@ -156,6 +157,7 @@ gather_csr_kernel(const float *__restrict__ W, const int *__restrict__ row_ptr, 
                   int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, float *__restrict__ dXv,
                   int *__restrict__ status) {
     __shared__ int s_rp[kWarps][33];
+    pdl_wait();  // W comes from the kernel launched before
     __shared__ uint32_t s_h[kWarps][32];
     __shared__ float s_sg[kWarps][32];
     const int lane = threadIdx.x & 31;
@@ -227,7 +229,9 @@ cudaError_t launch_gather_dense(const float *W, int n, int d, uint32_t B, Key ke
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(dX) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(W) & 15) == 0);
     record(ev, true, stream);
-    gather_dense_kernel<<<grid, kThreads, 0, stream>>>(W, n, d, B, key, row_offset, vec, dX);
+    const cudaError_t e = launch_after_previous(gather_dense_kernel, dim3(grid), dim3(kThreads), 0, stream, W, n, d, B,
+                                                key, row_offset, vec, dX);
+    if (e != cudaSuccess) return e;
     record(ev, false, stream);
     return cudaGetLastError();
 }
@@ -239,10 +243,10 @@ cudaError_t launch_gather_csr(const float *W, const int *row_ptr, const int *col
     const int nchunks = (n + 31) / 32;
     const int grid = max(1, min(gather_ctas(), (nchunks + kWarps - 1) / kWarps));
     record(ev, true, stream);
-    gather_csr_kernel<<<grid, kThreads, 0, stream>>>(W, row_ptr, col_idx, n, d, B, nnz, key, row_offset, dXv,
-                                                     status);
+    const cudaError_t e = launch_after_previous(gather_csr_kernel, dim3(grid), dim3(kThreads), 0, stream, W, row_ptr,
+                                                col_idx, n, d, B, nnz, key, row_offset, dXv, status);
     record(ev, false, stream);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace cg

@@ -12,6 +12,7 @@ namespace {
 __global__ void __launch_bounds__(256)
 row_argmax_argmin_kernel(const float *__restrict__ Z, int m, int d, int32_t *__restrict__ imax,
                          int32_t *__restrict__ imin) {
+    pdl_wait();  // Z comes from the split-K sum launched before
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (row >= m) return;
@@ -60,7 +61,9 @@ extern "C" cg_status cg_row_argmax_argmin(const float *Z, int32_t m, int32_t d, 
     using namespace cg;
     if (m < 0 || d < 1 || (m > 0 && (Z == nullptr || imax == nullptr || imin == nullptr))) return CG_ERR_INVALID_ARG;
     if (m == 0) return CG_OK;
-    row_argmax_argmin_kernel<<<(m + 7) / 8, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(Z, m, d, imax, imin);
+    const cudaError_t e = launch_after_previous(row_argmax_argmin_kernel, dim3((m + 7) / 8), dim3(256), 0,
+                                                reinterpret_cast<cudaStream_t>(stream), Z, m, d, imax, imin);
+    if (e != cudaSuccess) return CG_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
 }
 
