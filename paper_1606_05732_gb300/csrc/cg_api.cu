@@ -293,7 +293,7 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
             L.a_bytes = sx;
             break;
         case CG_OP_PLAIN_CSR:
-            L.b_bytes = static_cast<size_t>(plain_ctas(p.m, p.d)) * p.m * p.d * sizeof(float);
+            L.b_bytes = plain_partials_bytes(p.m, p.d);
             break;
         case CG_OP_SKETCH:
             L.c_bytes = scatter_scratch(p, nnz, &L.part);

@@ -183,8 +183,11 @@ cudaError_t launch_right_scatter(const int *row_ptr, const int *col_idx, const f
                                  int *status, const EventPair *ev, cudaStream_t stream);
 
 // ---- plain product (cg_plain.cu) ---------------------------------------------
+// Whether the plain product runs for m x d (in tiles of rows of G~ where the m x d
+// accumulator does not fit the shared memory), its CTAs, and its partials' bytes.
 bool plain_supported(int m, int d);
 int plain_ctas(int m, int d);
+size_t plain_partials_bytes(int m, int d);
 cudaError_t launch_plain_csr(const int *row_ptr, const int *col_idx, const float *vals, int n, int d, int m,
                              int nnz, Key key, int64_t row_offset, float *partials, float *Y, int *status,
                              const EventPair *ev, cudaStream_t stream);

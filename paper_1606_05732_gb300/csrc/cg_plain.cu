@@ -17,7 +17,9 @@
 // each lane finding its nonzero's row by binary search; each nonzero's m-wide update is
 // broadcast to the lanes by shuffles.  The kernel is specialised for the common m (8,
 // 16, 32, 64, 128) so that the per-nonzero loops have constant trip counts.  Each CTA
-// writes one m x d partial, summed in a fixed order afterwards.
+// writes one m x d partial, summed in a fixed order afterwards.  When m x d does not fit
+// the shared memory, the kernel runs once per tile of rows of G~ (and of Y), each launch
+// drawing only its own rows of G~ (no entry is drawn twice).
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -41,8 +43,8 @@ inline size_t plain_smem_bytes(int m, int d) {
 template <int M>
 __global__ void __launch_bounds__(kThreads, 4)  // at most 64 registers: four CTAs per SM
 plain_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
-                 int n, int d, int m_rt, int nnz, Key key, int64_t row_offset, int P, float *__restrict__ part,
-                 int *__restrict__ status) {
+                 int n, int d, int m_rt, int groups_total, int g_off, int nnz, Key key, int64_t row_offset, int P,
+                 float *__restrict__ part, int *__restrict__ status) {
     extern __shared__ __align__(16) float smem[];
     const int m = M > 0 ? M : m_rt;
     const int lane = threadIdx.x & 31;
@@ -106,12 +108,14 @@ plain_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_id
                 const int s1 = t1 / ngroups, g1 = t1 - s1 * ngroups;
                 const int row0 = (c << 5) + slot_lane[s0];
                 const int row1 = (c << 5) + (t1 < nq ? slot_lane[s1] : 0);
-                const float4 z0 = gauss_quad(key, kTagGTilde, static_cast<uint64_t>(ngroups),
-                                             static_cast<uint64_t>(row_offset + row0), static_cast<uint64_t>(g0));
+                // rows 4 (g_off + g) .. of the m_total x n Gaussian (groups_total groups)
+                const float4 z0 = gauss_quad(key, kTagGTilde, static_cast<uint64_t>(groups_total),
+                                             static_cast<uint64_t>(row_offset + row0),
+                                             static_cast<uint64_t>(g_off + g0));
                 float4 z1 = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (t1 < nq)
-                    z1 = gauss_quad(key, kTagGTilde, static_cast<uint64_t>(ngroups),
-                                    static_cast<uint64_t>(row_offset + row1), static_cast<uint64_t>(g1));
+                    z1 = gauss_quad(key, kTagGTilde, static_cast<uint64_t>(groups_total),
+                                    static_cast<uint64_t>(row_offset + row1), static_cast<uint64_t>(g_off + g1));
                 float *d0 = gbuf + s0 * m + 4 * g0;
                 if (4 * g0 + 0 < m) d0[0] = z0.x;
                 if (4 * g0 + 1 < m) d0[1] = z0.y;
@@ -193,8 +197,8 @@ plain_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_id
     }
 }
 
-using PlainKernel = void (*)(const int *, const int *, const float *, int, int, int, int, Key, int64_t, int, float *,
-                            int *);
+using PlainKernel = void (*)(const int *, const int *, const float *, int, int, int, int, int, int, Key, int64_t, int,
+                            float *, int *);
 
 PlainKernel plain_kernel_for(int m) {
     switch (m) {
@@ -207,11 +211,26 @@ PlainKernel plain_kernel_for(int m) {
     }
 }
 
+// Rows of G~ per launch: all m where the m x d accumulator fits, else the largest of
+// 128, 64, 32, 16, 8, 4 that fits (0 if none does).
+int plain_tile_rows(int m, int d) {
+    if (plain_smem_bytes(m, d) <= static_cast<size_t>(kSmemLimit)) return m;
+    for (int t : {128, 64, 32, 16, 8, 4})
+        if (t < m && plain_smem_bytes(t, d) <= static_cast<size_t>(kSmemLimit)) return t;
+    return 0;
+}
+
 }  // namespace
 
-bool plain_supported(int m, int d) { return plain_smem_bytes(m, d) <= static_cast<size_t>(kSmemLimit); }
+bool plain_supported(int m, int d) { return plain_tile_rows(m, d) > 0; }
+
+size_t plain_partials_bytes(int m, int d) {
+    const int mt = plain_tile_rows(m, d) > 0 ? plain_tile_rows(m, d) : m;
+    return static_cast<size_t>(plain_ctas(m, d)) * mt * d * sizeof(float);
+}
 
 int plain_ctas(int m, int d) {
+    m = plain_tile_rows(m, d) > 0 ? plain_tile_rows(m, d) : m;
     const int sms = num_sms() > 0 ? num_sms() : 148;
     const size_t per = plain_smem_bytes(m, d);
     int resident = static_cast<int>((227 * 1024) / (per + 1024));
@@ -225,19 +244,28 @@ int plain_ctas(int m, int d) {
 cudaError_t launch_plain_csr(const int *row_ptr, const int *col_idx, const float *vals, int n, int d, int m,
                              int nnz, Key key, int64_t row_offset, float *partials, float *Y, int *status,
                              const EventPair *ev, cudaStream_t stream) {
-    const size_t smem = plain_smem_bytes(m, d);
-    const PlainKernel kernel = plain_kernel_for(m);
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
+    const int mt = plain_tile_rows(m, d);
+    if (mt <= 0) return cudaErrorInvalidValue;
+    const int groups_total = (m + 3) / 4;
     const int nchunks = (n + 31) / 32;
     const int grid = max(1, min(plain_ctas(m, d), (nchunks + kWarps - 1) / kWarps));
-    record(ev, true, stream);
-    kernel<<<grid, kThreads, smem, stream>>>(row_ptr, col_idx, vals, n, d, m, nnz, key, row_offset, rows_per_pass(m),
-                                             partials, status);
-    record(ev, false, stream);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_reduce_splits(partials, grid, static_cast<int64_t>(m) * d, Y, stream);
+    // one launch (and one split sum into rows q0 .. q0 + rows of Y) per tile of rows of G~
+    for (int q0 = 0; q0 < m; q0 += mt) {
+        const int rows = min(mt, m - q0);
+        const size_t smem = plain_smem_bytes(rows, d);
+        const PlainKernel kernel = plain_kernel_for(rows);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        record(ev, q0 == 0, stream);
+        kernel<<<grid, kThreads, smem, stream>>>(row_ptr, col_idx, vals, n, d, rows, groups_total, q0 / 4, nnz, key,
+                                                 row_offset, rows_per_pass(rows), partials, status);
+        if (q0 + mt >= m) record(ev, false, stream);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_reduce_splits(partials, grid, static_cast<int64_t>(rows) * d, Y + static_cast<size_t>(q0) * d, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace cg

@@ -426,3 +426,18 @@ def test_largest_d_and_m(n, d, m, B, seed, precision):
     Yo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals)
     assert Y.shape == (m, d)
     assert rel(Y, Yo) < FP32_TOL
+
+
+@pytest.mark.parametrize("n,d,m,seed", [(3000, 300, 512, 61), (2000, 1000, 301, 62)])
+def test_plain_in_tiles_of_rows(n, d, m, seed):
+    """The plain product for an m x d accumulator larger than shared memory runs in tiles
+    of rows of G~ (512 x 300: four tiles of 128; 301 x 1000: nine tiles of 32 and a last
+    one of 13 rows, whose Gaussian group is partial); every row against the oracle."""
+    X = synth.csr_bernoulli(n, d, 0.05, seed=seed)
+    rp, ci, v = dev_csr(X)
+    plan = cg().CountGauss(n, d, m, 64, seed, row_offset=5)
+    Yp = plan.plain_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    want = oracle.plain_csr(seed, n, d, m, X.row_ptr, X.col_idx, X.vals, row_offset=5)
+    assert Yp.shape == (m, d)
+    assert rel(Yp, want) < FP32_TOL
