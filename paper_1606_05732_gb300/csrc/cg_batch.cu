@@ -95,6 +95,60 @@ __device__ __forceinline__ void prefetch_l2_range(const void *p, size_t bytes) {
     }
 }
 
+// Rows [first, min(first + 32 kCompactK, last)) of a very sparse instance, one non-empty
+// row per lane: the warp first reads the rows' offsets (coalesced, 32 rows per step) and
+// packs the indices of the non-empty ones into s_list (ballot order, so row order);
+// then lanes take them 32 at a time, hash them and walk their nonzeros.  A warp hashes
+// once per 32 non-empty rows instead of once per 32 rows (most rows of such instances
+// are empty).  Out-of-range column indices and malformed offsets are skipped and
+// reported through `bad`.
+constexpr int kCompactK = 8;
+
+__device__ __forceinline__ void scatter_lanes_compact(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                                                      const float *__restrict__ vals, int first, int last, int d,
+                                                      uint32_t B, int nnz, Key key, float *__restrict__ SX,
+                                                      int *s_list, int &bad) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int count = 0;
+#pragma unroll
+    for (int k = 0; k < kCompactK; ++k) {
+        const int i = first + 32 * k + lane;
+        const int beg = i < last ? __ldg(row_ptr + i) : 0;
+        int end = __shfl_down_sync(0xffffffffu, beg, 1);  // row_ptr[i + 1] from the next lane
+        if (i < last && (lane == 31 || i + 1 == last)) end = __ldg(row_ptr + i + 1);
+        bool live = false;
+        if (i < last) {
+            if (beg < 0 || end > nnz || beg > end)
+                bad = 1;  // malformed offsets: skip the row
+            else
+                live = beg < end;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, live);
+        if (live) s_list[count + __popc(mask & below)] = i;
+        count += __popc(mask);
+    }
+    __syncwarp();
+    for (int base = 0; base < count; base += 32) {
+        if (base + lane < count) {
+            const int i = s_list[base + lane];
+            const int beg = __ldg(row_ptr + i), end = __ldg(row_ptr + i + 1);
+            uint32_t h;
+            float sg;
+            hash_sign(key, static_cast<uint64_t>(i), B, h, sg);
+            const size_t row0 = static_cast<size_t>(h) * d;
+            for (int k = beg; k < end; ++k) {
+                const int j = __ldg(col_idx + k);
+                if (static_cast<unsigned>(j) < static_cast<unsigned>(d))
+                    atomicAdd(SX + row0 + j, sg * __ldg(vals + k));
+                else
+                    bad = 1;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -110,6 +164,7 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
     __shared__ int s_rp[kBWarps][33];
     __shared__ uint32_t s_h[kBWarps][32];
     __shared__ float s_sg[kBWarps][32];
+    __shared__ int s_list[kBWarps][32 * kCompactK];
     __shared__ int s_item, s_flag;
     const int t = threadIdx.x;
     const int w = t >> 5;
@@ -134,11 +189,12 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
                     prefetch_l2_range(I.vals + k0, static_cast<size_t>(k1 - k0) * sizeof(float));
                 }
             }
-            for (int first = item.a + w * 32; first < item.b; first += kBWarps * 32) {
-                if (I.lanes)  // warp-uniform
-                    scatter_lanes32<false, true>(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, 0,
-                                                 I.key, 0, I.SX, 0, bad);
-                else
+            if (I.lanes) {  // CTA-uniform
+                for (int first = item.a + w * 32 * kCompactK; first < item.b; first += kBWarps * 32 * kCompactK)
+                    scatter_lanes_compact(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, I.key, I.SX,
+                                          s_list[w], bad);
+            } else {
+                for (int first = item.a + w * 32; first < item.b; first += kBWarps * 32)
                     scatter_chunk32<false, true>(I.row_ptr, I.col_idx, I.vals, first, item.b, I.d, I.B, I.nnz, I.key,
                                                  0, I.SX, 0, s_rp[w], s_h[w], s_sg[w], bad);
             }
