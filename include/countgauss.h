@@ -105,10 +105,11 @@ typedef enum cg_option {
     CG_OPT_SCATTER_PASSES = 8, /* bucket-range passes of the atomic CSR scatter (each pass streams
                                  the CSR and reduces the rows of one range of buckets, keeping
                                  that range of SX in L2); 0 = automatic (one pass), 1..16 forced */
-    CG_OPT_SCATTER_ROWS = 9,  /* CSR rows per warp chunk of the scatter: 0 = automatic (the
-                                 smallest of 32, 64, 128 whose chunk holds about 96 nonzeros on
-                                 average; 256 in the deferred scatter for rows of under 1.5
-                                 nonzeros), 32, 64, 128 forced (rows staged in shared memory,
+    CG_OPT_SCATTER_ROWS = 9,  /* CSR rows per warp chunk of the scatter: 0 = automatic (one row
+                                 per lane for n <= 2^18 with under two nonzeros per row, where
+                                 latency rules; else the smallest of 32, 64, 128 whose chunk
+                                 holds about 96 nonzeros on average; 256 in the deferred scatter
+                                 for rows of under 1.5 nonzeros), 32, 64, 128 forced (rows staged in shared memory,
                                  nonzeros swept 32 at a time), 256 forced (deferred scatter only;
                                  the others take it as automatic), or 1 (one row per lane, each
                                  lane walking its own row; one-pass scatters only) */
