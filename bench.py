@@ -42,8 +42,8 @@ UNIT = "nnz/s"
 
 # dram bytes (read + write) per launch of the scatter kernel from one ncu capture of the
 # workload named, keyed by the sha256 of the kernel source it was taken on (null once the
-# source changes).  nmf_n16M_d64: 536.82 MB read + 3.23 MB written, captured at full size.
-NCU_TRAFFIC = {("ad38512167c92068", "nmf_n16M_d64"): 540_050_432}
+# source changes).  nmf_n16M_d64: 536.71 MB read + 3.23 MB written, captured at full size.
+NCU_TRAFFIC = {("802e40570ecb3b85", "nmf_n16M_d64"): 539_945_728}
 
 
 def parse_args():

@@ -33,6 +33,7 @@ sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     __shared__ float s_sg[kWarps][CH];
     const int w = threadIdx.x >> 5;
     const int nchunks = (n + CH - 1) / CH;
+    pdl_wait();  // SX may still be being zeroed by the kernel before this one
     const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
     int bad = 0;
     for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
@@ -59,23 +60,58 @@ int chunk_rows(int n, int nnz, int forced) {
 
 int chunk_height(int rows) { return rows == 1 ? 32 : rows; }
 
+template <bool FIXED, int ROWS>
+void launch_csr_rows_as(bool after_previous, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
+                        const float *vals, int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset,
+                        void *SX, const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
+    if (after_previous)
+        launch_after_previous(sketch_csr_kernel<FIXED, ROWS>, dim3(grid), dim3(kThreads), 0, stream, row_ptr, col_idx,
+                              vals, n, d, B, nnz, klo, key, row_offset, SX, maxbits, status, blo, bhi);
+    else
+        sketch_csr_kernel<FIXED, ROWS><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
+                                                                      row_offset, SX, maxbits, status, blo, bhi);
+}
+
+// `after_previous`: the scatter is launched as a programmatic dependent of the kernel
+// before it (which zeroes SX) and waits for it before its first reduction.
 template <bool FIXED>
 void launch_csr_rows(int rows, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
                      const float *vals, int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset,
-                     void *SX, const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
+                     void *SX, const int *maxbits, int *status, uint32_t blo, uint32_t bhi,
+                     bool after_previous = false) {
     if (rows == 1)
-        sketch_csr_kernel<FIXED, 0><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
-                                                                   key, row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 0>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
+                                     row_offset, SX, maxbits, status, blo, bhi);
     else if (rows == 128)
-        sketch_csr_kernel<FIXED, 128><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz,
-                                                                     klo, key, row_offset, SX, maxbits, status, blo,
-                                                                     bhi);
+        launch_csr_rows_as<FIXED, 128>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
+                                       row_offset, SX, maxbits, status, blo, bhi);
     else if (rows == 64)
-        sketch_csr_kernel<FIXED, 64><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
-                                                                    key, row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 64>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
+                                      row_offset, SX, maxbits, status, blo, bhi);
     else
-        sketch_csr_kernel<FIXED, 32><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
-                                                                    key, row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 32>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
+                                      row_offset, SX, maxbits, status, blo, bhi);
+}
+
+// Zero fill for a small SX ahead of the scatter.  A kernel rather than a memset, so that
+// the scatter can be launched as its programmatic dependent: the gap between two
+// launches is a visible share of a call that takes a few microseconds.  Values before
+// the first 16-byte boundary and after the last one are stored one by one.
+constexpr size_t kZeroKernelMaxBytes = size_t(8) << 20;
+
+__global__ void __launch_bounds__(kThreads) zero_fill_kernel(float *__restrict__ p, int64_t count) {
+    asm volatile("griddepcontrol.launch_dependents;");
+    const uint32_t mis = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p) & 15u);
+    int64_t head = mis ? static_cast<int64_t>((16u - mis) >> 2) : 0;
+    head = head < count ? head : count;
+    const int64_t body = (count - head) >> 2;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+    float4 *v = reinterpret_cast<float4 *>(p + head);
+    for (int64_t i = tid; i < body; i += stride) v[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    const int64_t rest = head + 4 * body;
+    if (tid < head) p[tid] = 0.0f;
+    if (tid < count - rest) p[rest + tid] = 0.0f;
 }
 
 // max |x| over the stored values, as the bit pattern of a non-negative float (whose
@@ -210,7 +246,22 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                      int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream,
                                      bool clear) {
-    cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
+    const size_t bytes = static_cast<size_t>(B) * d * sizeof(float);
+    // A small SX is zeroed by a kernel that the scatter follows as a programmatic
+    // dependent (not when the scatter alone is timed between events).
+    const bool zero_kernel = clear && n > 0 && bytes > 0 && bytes <= kZeroKernelMaxBytes && ev == nullptr;
+    cudaError_t e = cudaSuccess;
+    if (zero_kernel) {
+        const int64_t count = static_cast<int64_t>(bytes / sizeof(float));
+        const int64_t need4 = (count / 4 + kThreads - 1) / kThreads;
+        const int sms = num_sms();
+        const int64_t cap = static_cast<int64_t>(sms > 0 ? sms : 148) * 2;
+        const int zgrid = static_cast<int>(need4 < 1 ? 1 : (need4 < cap ? need4 : cap));
+        zero_fill_kernel<<<zgrid, kThreads, 0, stream>>>(SX, count);
+        e = cudaGetLastError();
+    } else if (clear) {
+        e = cudaMemsetAsync(SX, 0, bytes, stream);
+    }
     if (e != cudaSuccess || n == 0) return e;
     rows = chunk_rows(n, nnz, rows);
     const int nchunks = (n + chunk_height(rows) - 1) / chunk_height(rows);
@@ -228,7 +279,7 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
         const uint32_t blo = per * static_cast<uint32_t>(p);
         const uint32_t bhi = p == passes - 1 ? B : blo + per;
         launch_csr_rows<false>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, 0, key, row_offset, SX,
-                               nullptr, status, blo, bhi);
+                               nullptr, status, blo, bhi, zero_kernel && p == 0);
     }
     record(ev, false, stream);
     return cudaGetLastError();
