@@ -42,8 +42,8 @@ UNIT = "nnz/s"
 
 # dram bytes (read + write) per launch of the scatter kernel from one ncu capture of the
 # workload named, keyed by the sha256 of the kernel source it was taken on (null once the
-# source changes).  nmf_n16M_d64: 536.71 MB read + 3.23 MB written, captured at full size.
-NCU_TRAFFIC = {("802e40570ecb3b85", "nmf_n16M_d64"): 539_945_728}
+# source changes).  nmf_n16M_d64: 536.85 MB read + 3.27 MB written, captured at full size.
+NCU_TRAFFIC = {("19bef95f33b8d9bb", "nmf_n16M_d64"): 540_124_928}
 
 
 def parse_args():
@@ -67,8 +67,8 @@ def parse_args():
     ap.add_argument("--kl-sweep", action="store_true",
                     help="instead of the step: Theorem 1's KL / Pinsker bound and Lemma 5's distinguisher vs B")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
-    ap.add_argument("--rows", default="ladder,grad,batch,small,svm",
-                    help="comma list of the other rows to measure (ladder, grad, batch, small, svm)")
+    ap.add_argument("--rows", default="ladder,grad,batch,small,svm,wide",
+                    help="comma list of the other rows to measure (ladder, grad, batch, small, svm, wide)")
     return ap.parse_args()
 
 
@@ -248,11 +248,12 @@ def reduction_ceiling(dev, count, cells, reps=5):
             "how": "cg_diag_random_reductions: count fp32 adds at hashed positions of an SX-sized array"}
 
 
-def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small", "svm")):
+def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small", "svm", "wide")):
     """The other rows of the hot path, each on its own workload (sizes in synth.WORKLOADS):
     precision ladder and plain product on the largest workload, dense forward and
-    adjoint, the 96-instance batch, deterministic mode, the small case's latency, and
-    the right projection of the SVM application on the largest TechTC-shaped pair."""
+    adjoint, the 96-instance batch, deterministic mode, the small case's latency, the
+    right projection of the SVM application on the largest TechTC-shaped pair, and the
+    64-bit row offsets entry point (past 2^31 nonzeros)."""
     import numpy as np
     import torch
 
@@ -273,6 +274,40 @@ def measure_rows(dev, reps, which=("ladder", "grad", "batch", "small", "svm")):
         rows.update(_small_row(dev, reps, csr_dev, stream))
     if "svm" in which:
         rows.update(_svm_row(dev, reps, csr_dev, stream))
+    if "wide" in which:
+        rows.update(_wide_row(dev, reps, csr_dev, stream))
+    return rows
+
+
+def _wide_row(dev, reps, csr_dev, stream):
+    """cg_apply_csr_i64: on the headline input with its row offsets widened to int64
+    (against the int32 call), and on a 2^25 x 64 matrix of about 2.4e9 nonzeros (19 GB
+    of CSR drawn on the device), which 32-bit offsets cannot index."""
+    import torch
+
+    from paper_1606_05732_gb300 import countgauss, synth
+    rows = {}
+    X, w = synth.workload_csr("nmf_n16M_d64")
+    rp, ci, v = csr_dev(X)
+    rp64 = rp.long()
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"])
+    Y = torch.empty(w["m"], w["d"], dtype=torch.float32, device=dev)
+    ms32 = _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, stream)
+    ms64 = _time_calls(lambda: plan.apply_csr(rp64, ci, v, out=Y), reps, stream)
+    plan.check()
+    rows["wide_offsets_nmf_n16M_d64"] = {"int32_ms": ms32, "int64_ms": ms64, "nnz": X.nnz}
+    del rp, ci, v, rp64, X
+    n, d, m, B, seed = 1 << 25, 64, 32, 1 << 17, 37
+    rp, ci, v = synth.wide_csr_device(n, d, 72, seed, device=dev)
+    nnz = ci.numel()
+    plan = countgauss.CountGauss(n, d, m, B, seed)
+    Y = torch.empty(m, d, dtype=torch.float32, device=dev)
+    ms = _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), max(3, reps // 20), stream)
+    plan.check()
+    rows["wide_n32M_d64_2.4G_nnz"] = {"nnz": nnz, "ms_per_call": ms, "nnz_per_s": nnz / (ms / 1e3),
+                                      "csr_bytes": 8 * nnz + 8 * (n + 1)}
+    del rp, ci, v
+    torch.cuda.empty_cache()
     return rows
 
 

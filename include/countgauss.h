@@ -148,7 +148,8 @@ typedef enum cg_op {
     CG_OP_SKETCH = 5,         /* cg_sketch_csr / cg_sketch_dense alone */
     CG_OP_CONTRACT = 6,       /* cg_contract alone */
     CG_OP_APPLY_CSR_HOST = 7, /* cg_apply_csr_host */
-    CG_OP_APPLY_RIGHT_CSR = 8 /* cg_apply_right_csr */
+    CG_OP_APPLY_RIGHT_CSR = 8, /* cg_apply_right_csr */
+    CG_OP_APPLY_CSR_I64 = 9    /* cg_apply_csr_i64 */
 } cg_op;
 
 /* ---- plans ---------------------------------------------------------------- */
@@ -190,6 +191,22 @@ CG_API cg_status cg_plan_timing(cg_plan *plan, int32_t kernel, double *total_ms,
 CG_API cg_status cg_apply_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
                        const float *vals, int64_t nnz, float *Y,
                        void *ws, size_t ws_bytes, void *stream);
+
+/* cg_apply_csr for a matrix of 2^31 nonzeros or more: the same transform (Section 1.1;
+ * Algorithm 1 steps 1-2) with 64-bit row offsets, row_ptr int64[n+1] (device, 8-byte
+ * aligned), col_idx int32[nnz], vals fp32[nnz], 0 <= nnz <= 2^40.  The scatter is the
+ * one-pass atomic scatter (CG_OPT_SCATTER 0 or 1; CG_OPT_SCATTER_PASSES and
+ * CG_OPT_SCATTER_ROWS apply), each warp chunk of rows taking its offsets relative to its
+ * first nonzero.  Y (device, m x d) is overwritten.  Workspace:
+ * cg_workspace_size(CG_OP_APPLY_CSR_I64, nnz).  Errors: CG_ERR_INVALID_ARG for null or
+ * misaligned pointers or nnz out of range; CG_ERR_UNSUPPORTED with CG_OPT_DETERMINISTIC
+ * = 1 or CG_OPT_SCATTER 2 or 3.  Out-of-range column indices, out-of-range or decreasing
+ * row offsets, and a chunk of rows (at most 128 consecutive rows) holding more than
+ * 2^31 - 2^20 stored entries are reported through the status word, the entries concerned
+ * skipped. */
+CG_API cg_status cg_apply_csr_i64(cg_plan *plan, const int64_t *row_ptr, const int32_t *col_idx,
+                                  const float *vals, int64_t nnz, float *Y,
+                                  void *ws, size_t ws_bytes, void *stream);
 
 /* Y = G.(S.X) for dense X (device, n x d, row stride ldx >= d floats). */
 CG_API cg_status cg_apply_dense(cg_plan *plan, const float *X, int64_t ldx, float *Y,

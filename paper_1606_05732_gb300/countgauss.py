@@ -130,15 +130,18 @@ class CountGauss:
 
     # -- the transform --------------------------------------------------------
     def apply_csr(self, row_ptr, col_idx, vals, out=None) -> torch.Tensor:
-        """Y = G.(S.X) for CSR X (Section 1.1; Algorithm 1 steps 1-2)."""
-        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        """Y = G.(S.X) for CSR X (Section 1.1; Algorithm 1 steps 1-2).  row_ptr int32, or
+        int64 for a matrix of 2^31 nonzeros or more (cg_apply_csr_i64)."""
+        wide = torch.is_tensor(row_ptr) and row_ptr.dtype == torch.int64
+        row_ptr = _need(row_ptr, torch.int64 if wide else torch.int32, "row_ptr")
         col_idx = _need(col_idx, torch.int32, "col_idx")
         vals = _need(vals, torch.float32, "vals")
         dev = row_ptr.device
         nnz = col_idx.numel()
         Y = torch.empty(self.m, self.d, dtype=torch.float32, device=dev) if out is None else out
-        ws = self.workspace(_lib.OP_APPLY_CSR, nnz, dev)
-        _lib.check("cg_apply_csr", self._lib.cg_apply_csr(
+        op, name = (_lib.OP_APPLY_CSR_I64, "cg_apply_csr_i64") if wide else (_lib.OP_APPLY_CSR, "cg_apply_csr")
+        ws = self.workspace(op, nnz, dev)
+        _lib.check(name, getattr(self._lib, name)(
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Y), _ptr(ws), ws.numel(), _stream(dev)))
         return Y
 

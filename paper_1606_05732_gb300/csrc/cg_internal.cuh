@@ -91,6 +91,8 @@ constexpr size_t kStatusBytes = 256;
 constexpr int64_t kMaxNnz = (1LL << 31) - (1LL << 20);
 // Most rows of X, with the same margin for the kernels' 32-bit row indices.
 constexpr int64_t kMaxRows = (1LL << 31) - (1LL << 20);
+// Stored entries of a matrix given with 64-bit row offsets (cg_apply_csr_i64).
+constexpr int64_t kMaxNnz64 = 1LL << 40;
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
@@ -109,6 +111,12 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                      int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream,
                                      bool clear = true);
+// The same with 64-bit row offsets (a matrix of 2^31 nonzeros or more); each warp chunk of
+// rows holds at most kMaxChunkNnz nonzeros, or is skipped and reported as malformed.
+cudaError_t launch_sketch_csr_atomic_i64(const long long *row_ptr, const int *col_idx, const float *vals, int n,
+                                         int d, uint32_t B, long long nnz, Key key, int64_t row_offset, float *SX,
+                                         int *status, int ctas, int passes, int rows, const EventPair *ev,
+                                         cudaStream_t stream, bool clear = true);
 cudaError_t launch_sketch_dense_atomic(const float *X, int64_t ldx, int n, int d, uint32_t B, Key key,
                                        int64_t row_offset, float *SX, int *status, int ctas, const EventPair *ev,
                                        cudaStream_t stream, bool clear = true);

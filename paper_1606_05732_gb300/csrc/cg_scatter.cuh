@@ -21,6 +21,16 @@ __device__ __forceinline__ int ld_stream_i32(const int *p, uint64_t pol) {
     return v;
 }
 
+__device__ __forceinline__ long long ld_stream_i64(const long long *p, uint64_t pol) {
+    long long v;
+    asm volatile("ld.global.nc.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Largest number of nonzeros in one warp chunk of a matrix with 64-bit row offsets: the
+// chunk's offsets are taken relative to its first nonzero and swept in 32-bit integers.
+constexpr long long kMaxChunkNnz = (1LL << 31) - (1LL << 20);
+
 __device__ __forceinline__ float ld_stream_f32(const float *p, uint64_t pol) {
     float v;
     asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
@@ -72,23 +82,58 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, int F) {
 // bhi = B reduces every row.
 // With SKIP_EMPTY, empty rows get no bucket and sign: a warp whose rows are all empty
 // skips the hash (worth it for inputs with mostly empty rows).
-template <bool FIXED, int ROWS, bool SKIP_EMPTY = false>
-__device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+// RP is the type of the row offsets, nnz and klo: int, or long long for matrices of 2^31
+// nonzeros or more.  With long long the chunk's offsets are rebased to its first nonzero
+// (col_idx / vals are then read from that nonzero on) and kept in 32-bit integers; a
+// chunk of more than kMaxChunkNnz nonzeros is reported as malformed.
+template <bool FIXED, int ROWS, bool SKIP_EMPTY = false, typename RP = int>
+__device__ __forceinline__ void scatter_chunk(const RP *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                               const float *__restrict__ vals, int first, int n, int d, uint32_t B,
-                                              int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
-                                              int F, int *s_rp, uint32_t *s_h, float *s_sg, int &bad,
-                                              uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
+                                              RP nnz_in, RP klo_in, Key key, int64_t row_offset,
+                                              void *__restrict__ SX, int F, int *s_rp, uint32_t *s_h, float *s_sg,
+                                              int &bad, uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
     static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128, "chunk height");
     constexpr int R = ROWS / 32;
     const int lane = threadIdx.x & 31;
     const uint64_t pol = l2_evict_first_policy();
     const int last = min(first + ROWS, n);
-    const int end = __ldg(row_ptr + last);
+    int end, nnz, klo;
     int rp[R];
+    bool malformed = false;
+    if constexpr (sizeof(RP) == 4) {
+        nnz = nnz_in;
+        klo = klo_in;
+        end = __ldg(row_ptr + last);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {  // all row_ptr loads in flight before the hashing
-        const int i = first + r * 32 + lane;
-        rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
+        for (int r = 0; r < R; ++r) {  // all row_ptr loads in flight before the hashing
+            const int i = first + r * 32 + lane;
+            rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
+        }
+    } else {
+        const long long end64 = __ldg(row_ptr + last);
+        long long rp64[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = first + r * 32 + lane;
+            rp64[r] = i < n ? ld_stream_i64(row_ptr + i, pol) : end64;
+        }
+        const long long base = __shfl_sync(0xffffffffu, rp64[0], 0);  // row_ptr[first]
+        malformed = base < klo_in || end64 > nnz_in || end64 < base || end64 - base > kMaxChunkNnz;
+        const long long span = malformed ? 0 : end64 - base;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long rel = rp64[r] - base;
+            rp[r] = rel >= 0 && rel <= span ? static_cast<int>(rel) : -1;  // -1 breaks the order check
+            malformed |= rel < 0 || rel > span;
+        }
+        malformed = __any_sync(0xffffffffu, malformed);
+        end = static_cast<int>(span);
+        nnz = end;
+        klo = 0;
+        if (!malformed) {
+            col_idx += base - klo_in;
+            vals += base - klo_in;
+        }
     }
     if (SKIP_EMPTY) {
 #pragma unroll
@@ -113,7 +158,7 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
     bool ordered = true;
 #pragma unroll
     for (int r = 0; r < R; ++r) ordered &= s_rp[r * 32 + lane] <= s_rp[r * 32 + lane + 1];
-    if (beg < klo || end > nnz || !__all_sync(0xffffffffu, ordered)) {  // malformed row_ptr: skip the chunk
+    if (malformed || beg < klo || end > nnz || !__all_sync(0xffffffffu, ordered)) {  // malformed: skip the chunk
         bad = 1;
         __syncwarp();
         return;
@@ -165,16 +210,21 @@ __device__ __forceinline__ void scatter_chunk(const int *__restrict__ row_ptr, c
 // row; the lanes' loads of one step fall in the chunk's short, contiguous range of
 // col_idx / vals (indexed from klo as in scatter_chunk).  Out-of-range column indices
 // and malformed row offsets are skipped and reported through `bad`.
-template <bool FIXED, bool SKIP_EMPTY = false>
-__device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+// RP as in scatter_chunk (each lane walks its own row in RP arithmetic).
+template <bool FIXED, bool SKIP_EMPTY = false, typename RP = int>
+__device__ __forceinline__ void scatter_lanes32(const RP *__restrict__ row_ptr, const int *__restrict__ col_idx,
                                                 const float *__restrict__ vals, int first, int n, int d, uint32_t B,
-                                                int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
+                                                RP nnz, RP klo, Key key, int64_t row_offset, void *__restrict__ SX,
                                                 int F, int &bad, uint32_t blo = 0u, uint32_t bhi = 0xFFFFFFFFu) {
     const int lane = threadIdx.x & 31;
     const uint64_t pol = l2_evict_first_policy();
     const int i = first + lane;
-    int beg = i < n ? ld_stream_i32(row_ptr + i, pol) : 0;
-    int end = __shfl_down_sync(0xffffffffu, beg, 1);  // row_ptr[i + 1] from the next lane
+    RP beg = 0;
+    if constexpr (sizeof(RP) == 4)
+        beg = i < n ? ld_stream_i32(row_ptr + i, pol) : 0;
+    else
+        beg = i < n ? ld_stream_i64(row_ptr + i, pol) : 0;
+    RP end = __shfl_down_sync(0xffffffffu, beg, 1);  // row_ptr[i + 1] from the next lane
     if (i < n) {
         if (lane == 31 || i + 1 == n) end = __ldg(row_ptr + i + 1);
         if (beg < klo || end > nnz || beg > end) {  // malformed row offsets: skip the row
@@ -186,7 +236,7 @@ __device__ __forceinline__ void scatter_lanes32(const int *__restrict__ row_ptr,
         if (!SKIP_EMPTY || beg < end) hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
         if (h < blo || h >= bhi) end = beg;  // another pass reduces this row
         const size_t base = static_cast<size_t>(h) * d;
-        for (int k = beg; k < end; ++k) {
+        for (RP k = beg; k < end; ++k) {
             const int j = ld_stream_i32(col_idx + (k - klo), pol);
             const float v = ld_stream_f32(vals + (k - klo), pol);
             if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {

@@ -22,10 +22,11 @@ constexpr int kUnroll = 4;  // nonzeros in flight per lane
 // memory and swept nonzero by nonzero (scatter_chunk), or, with ROWS = 0, 32 rows of
 // one lane each (scatter_lanes32).  Each nonzero becomes one reduction into SX (fp32;
 // with FIXED, int64 fixed point).
-template <bool FIXED, int ROWS>
+// RP: the type of the row offsets (int, or long long for 2^31 nonzeros or more).
+template <bool FIXED, int ROWS, typename RP = int>
 __global__ void __launch_bounds__(kThreads)
-sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
-                  int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset, void *__restrict__ SX,
+sketch_csr_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
+                  int n, int d, uint32_t B, RP nnz, RP klo, Key key, int64_t row_offset, void *__restrict__ SX,
                   const int *__restrict__ maxbits, int *__restrict__ status, uint32_t blo, uint32_t bhi) {
     constexpr int CH = ROWS == 0 ? 32 : ROWS;
     __shared__ int s_rp[kWarps][ROWS == 0 ? 1 : ROWS + 1];
@@ -34,15 +35,15 @@ sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     const int w = threadIdx.x >> 5;
     const int nchunks = (n + CH - 1) / CH;
     pdl_wait();  // SX may still be being zeroed by the kernel before this one
-    const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
+    const int F = FIXED ? fixed_point_exponent(*maxbits, static_cast<int>(nnz)) : 0;
     int bad = 0;
     for (int c = blockIdx.x * kWarps + w; c < nchunks; c += gridDim.x * kWarps) {
         if constexpr (ROWS == 0)
-            scatter_lanes32<FIXED>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, klo, key, row_offset, SX, F, bad,
-                                   blo, bhi);
+            scatter_lanes32<FIXED, false, RP>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, klo, key, row_offset, SX,
+                                              F, bad, blo, bhi);
         else
-            scatter_chunk<FIXED, ROWS>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, klo, key, row_offset, SX, F,
-                                       s_rp[w], s_h[w], s_sg[w], bad, blo, bhi);
+            scatter_chunk<FIXED, ROWS, false, RP>(row_ptr, col_idx, vals, c * CH, n, d, B, nnz, klo, key, row_offset,
+                                                  SX, F, s_rp[w], s_h[w], s_sg[w], bad, blo, bhi);
     }
     if (bad) atomicOr(status, kStatusBounds);
 }
@@ -50,7 +51,7 @@ sketch_csr_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
 // Rows per warp chunk: `forced` (1 = one row per lane in chunks of 32, or 32, 64, 128
 // rows staged in shared memory) or, for 0, the smallest staged height whose chunk holds
 // about 96 nonzeros on average.
-int chunk_rows(int n, int nnz, int forced) {
+int chunk_rows(int n, int64_t nnz, int forced) {
     if (forced == 1 || forced == 32 || forced == 64 || forced == 128) return forced;
     const double per_row = n > 0 ? static_cast<double>(nnz) / n : 0.0;
     if (per_row * 32 >= 96.0) return 32;
@@ -60,37 +61,38 @@ int chunk_rows(int n, int nnz, int forced) {
 
 int chunk_height(int rows) { return rows == 1 ? 32 : rows; }
 
-template <bool FIXED, int ROWS>
-void launch_csr_rows_as(bool after_previous, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
-                        const float *vals, int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset,
+template <bool FIXED, int ROWS, typename RP>
+void launch_csr_rows_as(bool after_previous, int grid, cudaStream_t stream, const RP *row_ptr, const int *col_idx,
+                        const float *vals, int n, int d, uint32_t B, RP nnz, RP klo, Key key, int64_t row_offset,
                         void *SX, const int *maxbits, int *status, uint32_t blo, uint32_t bhi) {
     if (after_previous)
-        launch_after_previous(sketch_csr_kernel<FIXED, ROWS>, dim3(grid), dim3(kThreads), 0, stream, row_ptr, col_idx,
-                              vals, n, d, B, nnz, klo, key, row_offset, SX, maxbits, status, blo, bhi);
+        launch_after_previous(sketch_csr_kernel<FIXED, ROWS, RP>, dim3(grid), dim3(kThreads), 0, stream, row_ptr,
+                              col_idx, vals, n, d, B, nnz, klo, key, row_offset, SX, maxbits, status, blo, bhi);
     else
-        sketch_csr_kernel<FIXED, ROWS><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
-                                                                      row_offset, SX, maxbits, status, blo, bhi);
+        sketch_csr_kernel<FIXED, ROWS, RP><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                                                          key, row_offset, SX, maxbits, status, blo,
+                                                                          bhi);
 }
 
 // `after_previous`: the scatter is launched as a programmatic dependent of the kernel
 // before it (which zeroes SX) and waits for it before its first reduction.
-template <bool FIXED>
-void launch_csr_rows(int rows, int grid, cudaStream_t stream, const int *row_ptr, const int *col_idx,
-                     const float *vals, int n, int d, uint32_t B, int nnz, int klo, Key key, int64_t row_offset,
+template <bool FIXED, typename RP = int>
+void launch_csr_rows(int rows, int grid, cudaStream_t stream, const RP *row_ptr, const int *col_idx,
+                     const float *vals, int n, int d, uint32_t B, RP nnz, RP klo, Key key, int64_t row_offset,
                      void *SX, const int *maxbits, int *status, uint32_t blo, uint32_t bhi,
                      bool after_previous = false) {
     if (rows == 1)
-        launch_csr_rows_as<FIXED, 0>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
-                                     row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 0, RP>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
+                                         row_offset, SX, maxbits, status, blo, bhi);
     else if (rows == 128)
-        launch_csr_rows_as<FIXED, 128>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
-                                       row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 128, RP>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                           key, row_offset, SX, maxbits, status, blo, bhi);
     else if (rows == 64)
-        launch_csr_rows_as<FIXED, 64>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
-                                      row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 64, RP>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                          key, row_offset, SX, maxbits, status, blo, bhi);
     else
-        launch_csr_rows_as<FIXED, 32>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo, key,
-                                      row_offset, SX, maxbits, status, blo, bhi);
+        launch_csr_rows_as<FIXED, 32, RP>(after_previous, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, klo,
+                                          key, row_offset, SX, maxbits, status, blo, bhi);
 }
 
 // Zero fill for a small SX ahead of the scatter.  A kernel rather than a memset, so that
@@ -242,10 +244,12 @@ int sketch_default_ctas() {
     return (sms > 0 ? sms : 148) * (2048 / kThreads);
 }
 
-cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
-                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream,
-                                     bool clear) {
+namespace {
+
+template <typename RP>
+cudaError_t sketch_csr_atomic(const RP *row_ptr, const int *col_idx, const float *vals, int n, int d, uint32_t B,
+                              RP nnz, Key key, int64_t row_offset, float *SX, int *status, int ctas, int passes,
+                              int rows, const EventPair *ev, cudaStream_t stream, bool clear) {
     const size_t bytes = static_cast<size_t>(B) * d * sizeof(float);
     // A small SX is zeroed by a kernel that the scatter follows as a programmatic
     // dependent (not when the scatter alone is timed between events).
@@ -278,11 +282,29 @@ cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, con
     for (int p = 0; p < passes; ++p) {
         const uint32_t blo = per * static_cast<uint32_t>(p);
         const uint32_t bhi = p == passes - 1 ? B : blo + per;
-        launch_csr_rows<false>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, 0, key, row_offset, SX,
-                               nullptr, status, blo, bhi, zero_kernel && p == 0);
+        launch_csr_rows<false, RP>(rows, grid, stream, row_ptr, col_idx, vals, n, d, B, nnz, RP(0), key, row_offset,
+                                   SX, nullptr, status, blo, bhi, zero_kernel && p == 0);
     }
     record(ev, false, stream);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_csr_atomic(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                     int ctas, int passes, int rows, const EventPair *ev, cudaStream_t stream,
+                                     bool clear) {
+    return sketch_csr_atomic<int>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, status, ctas, passes,
+                                  rows, ev, stream, clear);
+}
+
+cudaError_t launch_sketch_csr_atomic_i64(const long long *row_ptr, const int *col_idx, const float *vals, int n,
+                                         int d, uint32_t B, long long nnz, Key key, int64_t row_offset, float *SX,
+                                         int *status, int ctas, int passes, int rows, const EventPair *ev,
+                                         cudaStream_t stream, bool clear) {
+    return sketch_csr_atomic<long long>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, status, ctas,
+                                        passes, rows, ev, stream, clear);
 }
 
 cudaError_t launch_sketch_csr_rows_chunk(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,

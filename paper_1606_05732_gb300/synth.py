@@ -18,6 +18,8 @@ densities and value distributions of the benchmark configurations:
 * ``techtc_pair``: a documents x words matrix shaped like one TechTC-300 pair of
   the SVM experiments (150-280 documents, 10,000-40,000 words); a shape stand-in,
   not the dataset.
+* ``wide_csr_device``: a CSR matrix of 2^31 nonzeros or more, drawn on the GPU
+  (torch's Philox-based CUDA generator, seeded), with int64 row offsets.
 """
 from __future__ import annotations
 
@@ -212,3 +214,21 @@ def sample_rows(m: int, seed: int, groups: int = 2) -> np.ndarray:
         chosen.add(int(rng.integers(0, ngroups)))
     rows = [r for g in sorted(chosen) for r in range(4 * g, min(4 * g + 4, m))]
     return np.asarray(rows, np.int64)
+
+
+def wide_csr_device(n: int, d: int, mean_row: int, seed: int, device="cuda"):
+    """(row_ptr int64[n+1], col_idx int32[nnz], vals float32[nnz]) on `device`: row
+    lengths uniform in [0, 2 mean_row], columns uniform in [0, d) (a row may repeat a
+    column; such entries are summed), values U[0,1).  Drawn with a seeded torch
+    generator on the device, for matrices too large to build on the host."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    lengths = torch.randint(0, 2 * mean_row + 1, (n,), dtype=torch.int64, device=device, generator=g)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(lengths, 0, out=row_ptr[1:])
+    del lengths
+    nnz = int(row_ptr[-1].item())
+    col_idx = torch.randint(0, d, (nnz,), dtype=torch.int32, device=device, generator=g)
+    vals = torch.rand(nnz, dtype=torch.float32, device=device, generator=g)
+    return row_ptr, col_idx, vals

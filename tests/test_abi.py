@@ -84,7 +84,7 @@ def test_options_and_workspace(lib):
         for x in bad:
             assert lib.cg_plan_set_option(h, opt, x) == 1
     sz = ctypes.c_size_t()
-    for op in range(9):
+    for op in range(10):
         assert lib.cg_workspace_size(h, op, 1000, ctypes.byref(sz)) == 0
         assert sz.value >= 256 and sz.value % 256 == 0
     assert lib.cg_workspace_size(h, 42, 0, ctypes.byref(sz)) == 1
@@ -122,6 +122,31 @@ def test_host_side_argument_errors_launch_nothing(lib):
     # accumulating into SX is not offered with the deterministic (fixed-point) scatter
     assert lib.cg_plan_set_option(h, 12, 1) == 0
     assert lib.cg_sketch_csr(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
+    lib.cg_plan_destroy(h)
+
+
+def test_wide_offsets_argument_errors_launch_nothing(lib):
+    """cg_apply_csr_i64 (64-bit row offsets): its host-side checks, before any CUDA call."""
+    st, h = _plan(lib)
+    P = ctypes.c_void_p
+    fake = P(1 << 20)
+    assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3  # workspace too small
+    assert lib.cg_apply_csr_i64(h, fake, fake, fake, -1, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr_i64(h, fake, fake, fake, (1 << 40) + 1, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr_i64(h, P(0), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr_i64(h, P((1 << 20) + 4), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1  # 4-aligned
+    assert lib.cg_apply_csr_i64(h, fake, P(0), fake, 10, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
+    # the deterministic, deferred and partitioned scatters take 32-bit offsets only
+    for opt, val in ((2, 1), (7, 3), (7, 2)):
+        assert lib.cg_plan_set_option(h, opt, val) == 0
+        assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
+        assert lib.cg_plan_set_option(h, opt, 0) == 0
+    # workspace: SX and the split-K partials, no scatter scratch, whatever nnz
+    sz, sz2 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.cg_workspace_size(h, 9, 10, ctypes.byref(sz)) == 0
+    assert lib.cg_workspace_size(h, 9, 1 << 33, ctypes.byref(sz2)) == 0
+    assert sz.value == sz2.value >= 256 + 16 * 4 * 4
     lib.cg_plan_destroy(h)
 
 

@@ -393,10 +393,16 @@ def test_bad_column_index_is_reported():
 
 
 def test_argument_errors_raise():
+    """Wrong dtypes are refused before the call (row offsets int32 or int64, column
+    indices int32, values float32)."""
     plan = cg().CountGauss(10, 4, 4, 8, 1)
-    rp = torch.zeros(11, dtype=torch.int64, device="cuda")
-    with pytest.raises(TypeError):
-        plan.apply_csr(rp, rp.int(), torch.zeros(0, device="cuda"))
+    rp = torch.zeros(11, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(0, dtype=torch.int32, device="cuda")
+    v = torch.zeros(0, device="cuda")
+    for args in ((rp.short(), ci, v), (rp.double(), ci, v), (rp, ci.long(), v), (rp.long(), ci.long(), v),
+                 (rp, ci, v.double())):
+        with pytest.raises(TypeError):
+            plan.apply_csr(*args)
 
 
 def test_diag_random_reductions_adds_exactly_count():

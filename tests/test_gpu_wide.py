@@ -1,0 +1,131 @@
+"""cg_apply_csr_i64: the transform Y = G.(S.X) (Section 1.1; Algorithm 1 steps 1-2) for
+CSR matrices given with 64-bit row offsets, i.e. of 2^31 nonzeros or more.
+
+Parity with the FP64 oracle at sizes it finishes in seconds (several chunks of rows and
+a ragged tail, every chunk height); at 2.4e9 nonzeros (past 2^31), agreement with the
+32-bit path applied to row blocks with their global row offsets, which is the same
+transform by linearity (h and sigma depend on the global row index only).  Malformed
+offsets are reported through the status word and skipped.  Bar: relative Frobenius
+error 1e-5 (FP32).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_05732_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def cg():
+    from paper_1606_05732_gb300 import countgauss
+    return countgauss
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def dev_csr64(X):
+    return (torch.from_numpy(X.row_ptr.astype(np.int64)).cuda(),
+            torch.from_numpy(X.col_idx.astype(np.int32)).cuda(),
+            torch.from_numpy(X.vals.astype(np.float32)).cuda())
+
+
+@pytest.mark.parametrize("rows", [0, 1, 32, 64, 128])
+@pytest.mark.parametrize("n,d,m,B,seed,per_row", [(70001, 37, 13, 3001, 31, 6), (4099, 64, 32, 512, 32, 64),
+                                                  (100_000, 16, 8, 4096, 33, 1)])
+def test_parity_with_oracle(n, d, m, B, seed, per_row, rows):
+    """Ragged rows (empty ones, full ones), every chunk height, a row offset."""
+    X = synth.csr_ragged(n, d, seed=seed, max_row=per_row)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter_rows=rows, row_offset=777)
+    Y = plan.apply_csr(*dev_csr64(X)).cpu().numpy()
+    plan.check()
+    Yo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=777)
+    assert rel(Y, Yo) < FP32_TOL
+
+
+@pytest.mark.parametrize("passes", [2, 5])
+def test_bucket_range_passes(passes):
+    n, d, m, B, seed = 50_000, 24, 16, 2048, 34
+    X = synth.csr_bernoulli(n, d, 0.1, seed)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter_passes=passes)
+    Y = plan.apply_csr(*dev_csr64(X)).cpu().numpy()
+    plan.check()
+    assert rel(Y, oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals)) < FP32_TOL
+
+
+def test_empty_matrix_and_empty_rows():
+    n, d, m, B, seed = 1000, 8, 4, 64, 35
+    plan = cg().CountGauss(n, d, m, B, seed)
+    rp = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    ci = torch.zeros(0, dtype=torch.int32, device="cuda")
+    v = torch.zeros(0, dtype=torch.float32, device="cuda")
+    Y = plan.apply_csr(rp, ci, v)
+    plan.check()
+    assert float(Y.abs().max()) == 0.0
+
+
+def test_same_as_32_bit_offsets():
+    """The two entry points compute the same transform (up to FP32 summation order)."""
+    X, w = synth.workload_csr("nmf_n16M_d64", scale_rows=1 / 64)
+    rp64, ci, v = dev_csr64(X)
+    plan = cg().CountGauss(X.n, X.d, w["m"], w["B"], w["seed"])
+    Y64 = plan.apply_csr(rp64, ci, v).cpu().numpy()
+    Y32 = plan.apply_csr(rp64.int(), ci, v).cpu().numpy()
+    plan.check()
+    assert rel(Y64, Y32) < FP32_TOL
+
+
+@pytest.mark.parametrize("rows", [1, 32, 128])
+def test_malformed_offsets_are_reported(rows):
+    from paper_1606_05732_gb300 import _lib
+    n, d, m, B, seed = 20_000, 16, 8, 1024, 36
+    X = synth.csr_ragged(n, d, seed=7, max_row=4)
+    rp, ci, v = dev_csr64(X)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter_rows=rows)
+    bad = rp.clone()
+    bad[n // 2], bad[n // 2 + 1] = rp[n // 2 + 1].item() + 1, rp[n // 2].item()  # decreasing
+    plan.apply_csr(bad, ci, v)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    bad = rp.clone()
+    bad[n] = X.nnz + 5  # past nnz
+    plan.apply_csr(bad, ci, v)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    bad = rp.clone()
+    bad[7] = -(1 << 40)  # far below the first nonzero
+    plan.apply_csr(bad, ci, v)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    plan.apply_csr(rp, ci, v)
+    plan.check()
+
+
+def test_past_2_pow_31_nonzeros_matches_row_blocks():
+    """2^25 rows x 64 columns with 72 nonzeros per row on average: about 2.4e9 nonzeros
+    (19 GB of CSR), past what 32-bit offsets hold.  Equals the sum of the 32-bit path
+    over two row blocks, each with its global row offset."""
+    n, d, m, B, seed = 1 << 25, 64, 32, 1 << 17, 37
+    rp, ci, v = synth.wide_csr_device(n, d, 72, seed)
+    nnz = ci.numel()
+    assert nnz > (1 << 31)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    Y = plan.apply_csr(rp, ci, v)
+    plan.check()
+    Yb = torch.zeros_like(Y)
+    cut = n // 2
+    for r0, r1 in ((0, cut), (cut, n)):
+        k0, k1 = int(rp[r0].item()), int(rp[r1].item())
+        assert k1 - k0 < (1 << 31) - (1 << 20)
+        part = cg().CountGauss(r1 - r0, d, m, B, seed, row_offset=r0)
+        Yb += part.apply_csr((rp[r0:r1 + 1] - k0).int(), ci[k0:k1], v[k0:k1])
+        part.check()
+    assert rel(Y.cpu().numpy(), Yb.cpu().numpy()) < FP32_TOL
