@@ -220,6 +220,18 @@ CG_API cg_status cg_apply_adjoint(cg_plan *plan, const float *dY, const int32_t 
                            const int32_t *col_idx, int64_t nnz, float *dX,
                            void *ws, size_t ws_bytes, void *stream);
 
+/* cg_apply_adjoint at the stored entries of a CSR pattern with int64 row offsets (2^31
+ * nonzeros or more; see cg_apply_csr_i64): dXv[k] = sigma(i).W[h(i), col_idx[k]] for
+ * each stored entry k of row i, W = G^T.dY (B x d) in ws.  row_ptr int64[n+1] (device,
+ * 8-byte aligned), col_idx int32[nnz], dXv fp32[nnz] (device) overwritten, 0 <= nnz <=
+ * 2^40.  Workspace: cg_workspace_size(CG_OP_ADJOINT_CSR, nnz).  Errors:
+ * CG_ERR_INVALID_ARG for null or misaligned pointers or nnz out of range; out-of-range
+ * column indices and out-of-range or decreasing row offsets are reported through the
+ * status word (the entries concerned are skipped). */
+CG_API cg_status cg_apply_adjoint_i64(cg_plan *plan, const float *dY, const int64_t *row_ptr,
+                                      const int32_t *col_idx, int64_t nnz, float *dXv,
+                                      void *ws, size_t ws_bytes, void *stream);
+
 /* The random projection of the SVM application (Section 9, the theorem on the margin;
  * Table 1 times it): Z = A.R with R = T^T, for a CSR matrix A with one row per sample
  * and one column per feature, i.e. A = X^T in the plan's terms.  A has d rows and n

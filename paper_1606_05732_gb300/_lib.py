@@ -53,6 +53,7 @@ SIGNATURES = {
     "cg_apply_csr_noalloc": [P, P, P, P, I64, P, P],
     "cg_apply_dense": [P, P, I64, P, P, SZ, P],
     "cg_apply_adjoint": [P, P, P, P, I64, P, P, SZ, P],
+    "cg_apply_adjoint_i64": [P, P, P, P, I64, P, P, SZ, P],
     "cg_plain_gaussian_apply": [P, P, P, P, I64, P, P, SZ, P],
     "cg_sketch_csr": [P, P, P, P, I64, P, P, SZ, P],
     "cg_sketch_dense": [P, P, I64, P, P, SZ, P],

@@ -202,19 +202,23 @@ class CountGauss:
         return Y
 
     def adjoint(self, dY, row_ptr=None, col_idx=None, out=None) -> torch.Tensor:
-        """dX = S^T.(G^T.dY): dense n x d, or nnz values at a CSR pattern."""
+        """dX = S^T.(G^T.dY): dense n x d, or nnz values at a CSR pattern (row_ptr int32,
+        or int64 for 2^31 nonzeros or more: cg_apply_adjoint_i64)."""
         dY = _need(dY, torch.float32, "dY")
         dev = dY.device
+        name = "cg_apply_adjoint"
         if row_ptr is None:
             dX = torch.empty(self.n, self.d, dtype=torch.float32, device=dev) if out is None else out
             nnz, op = 0, _lib.OP_ADJOINT_DENSE
         else:
-            row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+            wide = torch.is_tensor(row_ptr) and row_ptr.dtype == torch.int64
+            row_ptr = _need(row_ptr, torch.int64 if wide else torch.int32, "row_ptr")
             col_idx = _need(col_idx, torch.int32, "col_idx")
             nnz, op = col_idx.numel(), _lib.OP_ADJOINT_CSR
+            name = "cg_apply_adjoint_i64" if wide else name
             dX = torch.empty(nnz, dtype=torch.float32, device=dev) if out is None else out
         ws = self.workspace(op, nnz, dev)
-        _lib.check("cg_apply_adjoint", self._lib.cg_apply_adjoint(
+        _lib.check(name, getattr(self._lib, name)(
             self._h, _ptr(dY), _ptr(row_ptr), _ptr(col_idx), nnz, _ptr(dX), _ptr(ws), ws.numel(), _stream(dev)))
         return dX
 

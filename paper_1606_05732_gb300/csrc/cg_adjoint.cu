@@ -151,12 +151,14 @@ gather_dense_kernel(const float *__restrict__ W, int n, int d, uint32_t B, Key k
     }
 }
 
-// dX_k = sigma(i) W[h(i), col_idx[k]] for the stored entries of CSR rows.
+// dX_k = sigma(i) W[h(i), col_idx[k]] for the stored entries of CSR rows.  RP is the
+// type of the row offsets and nonzero indices: int, or long long for 2^31 nonzeros or more.
+template <typename RP>
 __global__ void __launch_bounds__(kThreads)
-gather_csr_kernel(const float *__restrict__ W, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
-                  int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, float *__restrict__ dXv,
+gather_csr_kernel(const float *__restrict__ W, const RP *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                  int n, int d, uint32_t B, RP nnz, Key key, int64_t row_offset, float *__restrict__ dXv,
                   int *__restrict__ status) {
-    __shared__ int s_rp[kWarps][33];
+    __shared__ RP s_rp[kWarps][33];
     pdl_wait();  // W comes from the kernel launched before
     __shared__ uint32_t s_h[kWarps][32];
     __shared__ float s_sg[kWarps][32];
@@ -168,8 +170,8 @@ gather_csr_kernel(const float *__restrict__ W, const int *__restrict__ row_ptr, 
         const int first = c << 5;
         const int i = first + lane;
         const int last = min(first + 32, n);
-        const int end = __ldg(row_ptr + last);
-        int rp = end;
+        const RP end = __ldg(row_ptr + last);
+        RP rp = end;
         uint32_t h = 0;
         float sg = 0.0f;
         if (i < n) {
@@ -180,13 +182,13 @@ gather_csr_kernel(const float *__restrict__ W, const int *__restrict__ row_ptr, 
         s_h[w][lane] = h;
         s_sg[w][lane] = sg;
         __syncwarp();
-        const int beg = s_rp[w][0];
+        const RP beg = s_rp[w][0];
         if (beg < 0 || end > nnz || beg > end) {
             bad = 1;
             __syncwarp();
             continue;
         }
-        for (int k = beg + lane; k < end; k += 32) {
+        for (RP k = beg + lane; k < end; k += 32) {
             int lo = 0;
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1)
@@ -236,17 +238,34 @@ cudaError_t launch_gather_dense(const float *W, int n, int d, uint32_t B, Key ke
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_csr(const float *W, const int *row_ptr, const int *col_idx, int n, int d, uint32_t B,
-                              int nnz, Key key, int64_t row_offset, float *dXv, int *status, const EventPair *ev,
-                              cudaStream_t stream) {
+namespace {
+
+template <typename RP>
+cudaError_t gather_csr(const float *W, const RP *row_ptr, const int *col_idx, int n, int d, uint32_t B, RP nnz,
+                       Key key, int64_t row_offset, float *dXv, int *status, const EventPair *ev,
+                       cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
     const int nchunks = (n + 31) / 32;
     const int grid = max(1, min(gather_ctas(), (nchunks + kWarps - 1) / kWarps));
     record(ev, true, stream);
-    const cudaError_t e = launch_after_previous(gather_csr_kernel, dim3(grid), dim3(kThreads), 0, stream, W, row_ptr,
-                                                col_idx, n, d, B, nnz, key, row_offset, dXv, status);
+    const cudaError_t e = launch_after_previous(gather_csr_kernel<RP>, dim3(grid), dim3(kThreads), 0, stream, W,
+                                                row_ptr, col_idx, n, d, B, nnz, key, row_offset, dXv, status);
     record(ev, false, stream);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gather_csr(const float *W, const int *row_ptr, const int *col_idx, int n, int d, uint32_t B,
+                              int nnz, Key key, int64_t row_offset, float *dXv, int *status, const EventPair *ev,
+                              cudaStream_t stream) {
+    return gather_csr<int>(W, row_ptr, col_idx, n, d, B, nnz, key, row_offset, dXv, status, ev, stream);
+}
+
+cudaError_t launch_gather_csr_i64(const float *W, const long long *row_ptr, const int *col_idx, int n, int d,
+                                  uint32_t B, long long nnz, Key key, int64_t row_offset, float *dXv, int *status,
+                                  const EventPair *ev, cudaStream_t stream) {
+    return gather_csr<long long>(W, row_ptr, col_idx, n, d, B, nnz, key, row_offset, dXv, status, ev, stream);
 }
 
 }  // namespace cg

@@ -790,6 +790,27 @@ cg_status cg_apply_adjoint(cg_plan *p, const float *dY, const int32_t *row_ptr, 
                                          p->row_offset, dX, timing_pair(p, CG_KERNEL_GATHER), st));
 }
 
+cg_status cg_apply_adjoint_i64(cg_plan *p, const float *dY, const int64_t *row_ptr, const int32_t *col_idx,
+                               int64_t nnz, float *dXv, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_apply_adjoint_i64");
+    if (p == nullptr || dY == nullptr || misaligned(dY, 4) || misaligned(dXv, 4)) return CG_ERR_INVALID_ARG;
+    if (nnz < 0 || nnz > kMaxNnz64 || row_ptr == nullptr || misaligned(row_ptr, 8)) return CG_ERR_INVALID_ARG;
+    if (nnz > 0 && (col_idx == nullptr || dXv == nullptr || misaligned(col_idx, 4))) return CG_ERR_INVALID_ARG;
+    cg_status s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_ADJOINT_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    float *W = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    const Key key = make_key(p->seed);
+    if ((s = from_cuda(launch_adjoint_w(dY, p->m, p->d, p->B, key, W, timing_pair(p, CG_KERNEL_ADJOINT_W), st))) !=
+        CG_OK)
+        return s;
+    return from_cuda(launch_gather_csr_i64(W, reinterpret_cast<const long long *>(row_ptr), col_idx,
+                                           static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
+                                           static_cast<long long>(nnz), key, p->row_offset, dXv, status_word(ws),
+                                           timing_pair(p, CG_KERNEL_GATHER), st));
+}
+
 cg_status cg_plain_gaussian_apply(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                                   int64_t nnz, float *Y, void *ws, size_t ws_bytes, void *stream) {
     cg::NvtxRange nvtx_range("cg_plain_gaussian_apply");

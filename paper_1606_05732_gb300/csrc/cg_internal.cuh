@@ -208,6 +208,9 @@ cudaError_t launch_gather_dense(const float *W, int n, int d, uint32_t B, Key ke
 cudaError_t launch_gather_csr(const float *W, const int *row_ptr, const int *col_idx, int n, int d, uint32_t B,
                               int nnz, Key key, int64_t row_offset, float *dXv, int *status, const EventPair *ev,
                               cudaStream_t stream);
+cudaError_t launch_gather_csr_i64(const float *W, const long long *row_ptr, const int *col_idx, int n, int d,
+                                  uint32_t B, long long nnz, Key key, int64_t row_offset, float *dXv, int *status,
+                                  const EventPair *ev, cudaStream_t stream);
 
 // ---- generator dumps (cg_api.cu) ---------------------------------------------
 cudaError_t launch_generate_words(Key key, uint32_t tag, uint64_t idx0, int64_t count, uint32_t *words,

@@ -142,6 +142,14 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
         assert lib.cg_plan_set_option(h, opt, val) == 0
         assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
         assert lib.cg_plan_set_option(h, opt, 0) == 0
+    # the adjoint at the stored entries: nnz range, null / misaligned pointers
+    assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, -1, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, (1 << 40) + 1, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_adjoint_i64(h, fake, P(0), fake, 10, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_adjoint_i64(h, fake, P((1 << 20) + 4), fake, 10, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_adjoint_i64(h, P(0), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
     # workspace: SX and the split-K partials, no scatter scratch, whatever nnz
     sz, sz2 = ctypes.c_size_t(), ctypes.c_size_t()
     assert lib.cg_workspace_size(h, 9, 10, ctypes.byref(sz)) == 0

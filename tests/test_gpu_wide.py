@@ -1,12 +1,14 @@
-"""cg_apply_csr_i64: the transform Y = G.(S.X) (Section 1.1; Algorithm 1 steps 1-2) for
-CSR matrices given with 64-bit row offsets, i.e. of 2^31 nonzeros or more.
+"""cg_apply_csr_i64 and cg_apply_adjoint_i64: the transform Y = G.(S.X) (Section 1.1;
+Algorithm 1 steps 1-2) and its adjoint at the stored entries, for CSR matrices given with
+64-bit row offsets, i.e. of 2^31 nonzeros or more.
 
 Parity with the FP64 oracle at sizes it finishes in seconds (several chunks of rows and
 a ragged tail, every chunk height); at 2.4e9 nonzeros (past 2^31), agreement with the
 32-bit path applied to row blocks with their global row offsets, which is the same
 transform by linearity (h and sigma depend on the global row index only).  Malformed
 offsets are reported through the status word and skipped.  Bar: relative Frobenius
-error 1e-5 (FP32).
+error 1e-5 (FP32); the adjoint's values are the same arithmetic as the 32-bit path's, so
+the two agree bit for bit.
 """
 import numpy as np
 import pytest
@@ -129,3 +131,70 @@ def test_past_2_pow_31_nonzeros_matches_row_blocks():
         Yb += part.apply_csr((rp[r0:r1 + 1] - k0).int(), ci[k0:k1], v[k0:k1])
         part.check()
     assert rel(Y.cpu().numpy(), Yb.cpu().numpy()) < FP32_TOL
+
+
+@pytest.mark.parametrize("n,d,m,B,seed,per_row", [(70001, 37, 13, 3001, 41, 6), (4099, 64, 32, 512, 42, 64)])
+def test_adjoint_parity_with_oracle(n, d, m, B, seed, per_row):
+    X = synth.csr_ragged(n, d, seed=seed, max_row=per_row)
+    rp, ci, _ = dev_csr64(X)
+    dYn = np.random.default_rng(seed).standard_normal((m, d)).astype(np.float32)
+    dY = torch.from_numpy(dYn).cuda()
+    plan = cg().CountGauss(n, d, m, B, seed, row_offset=99)
+    dXv = plan.adjoint(dY, rp, ci)
+    plan.check()
+    assert rel(dXv.cpu().numpy(), oracle.adjoint_csr(seed, n, m, B, X.row_ptr, X.col_idx, dYn, row_offset=99)) \
+        < FP32_TOL
+    assert torch.equal(dXv, plan.adjoint(dY, rp.int(), ci))  # same W, same products
+
+
+def test_autograd_with_wide_offsets():
+    """The CSR autograd function takes int64 offsets in both directions."""
+    n, d, m, B, seed = 30_000, 16, 8, 1024, 43
+    X = synth.csr_bernoulli(n, d, 0.05, seed)
+    rp, ci, v = dev_csr64(X)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    grads = []
+    for offsets in (rp, rp.int()):
+        vals = v.clone().requires_grad_(True)
+        Y = cg().countgauss_csr(vals, offsets, ci, plan)
+        (Y * Y).sum().backward()
+        grads.append(vals.grad)
+    plan.check()
+    assert rel(grads[0].cpu().numpy(), grads[1].cpu().numpy()) < FP32_TOL
+
+
+def test_adjoint_malformed_offsets_are_reported():
+    from paper_1606_05732_gb300 import _lib
+    n, d, m, B, seed = 5000, 8, 4, 256, 44
+    X = synth.csr_ragged(n, d, seed=9, max_row=4)
+    rp, ci, _ = dev_csr64(X)
+    dY = torch.ones(m, d, device="cuda")
+    plan = cg().CountGauss(n, d, m, B, seed)
+    bad = rp.clone()
+    bad[n] = X.nnz + 1
+    plan.adjoint(dY, bad, ci)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    plan.adjoint(dY, rp, ci)
+    plan.check()
+
+
+def test_adjoint_past_2_pow_31_nonzeros_matches_row_blocks():
+    """The gradient at 2.4e9 stored entries equals, bit for bit, the 32-bit path's on two
+    row blocks with their global row offsets."""
+    n, d, m, B, seed = 1 << 25, 64, 32, 1 << 17, 45
+    rp, ci, v = synth.wide_csr_device(n, d, 72, seed)
+    del v
+    assert ci.numel() > (1 << 31)
+    dY = torch.randn(m, d, device="cuda", generator=torch.Generator(device="cuda").manual_seed(seed))
+    plan = cg().CountGauss(n, d, m, B, seed)
+    dXv = plan.adjoint(dY, rp, ci)
+    plan.check()
+    cut = n // 2
+    for r0, r1 in ((0, cut), (cut, n)):
+        k0, k1 = int(rp[r0].item()), int(rp[r1].item())
+        part = cg().CountGauss(r1 - r0, d, m, B, seed, row_offset=r0)
+        blk = part.adjoint(dY, (rp[r0:r1 + 1] - k0).int(), ci[k0:k1])
+        part.check()
+        assert torch.equal(dXv[k0:k1], blk)
+        del blk
