@@ -257,7 +257,8 @@ CG_API cg_status cg_plain_gaussian_apply(cg_plan *plan, const int32_t *row_ptr, 
 /* ---- stages (for stage-wise checks and measurement) ----------------------- */
 
 /* SX = S.X alone (Section 1.1: O(nnz(X)) scatter).  SX (device, B x d) is
- * overwritten, or added into with CG_OPT_ACCUMULATE = 1.  Honours CG_OPT_DETERMINISTIC. */
+ * overwritten, or added into with CG_OPT_ACCUMULATE = 1.  Honours CG_OPT_DETERMINISTIC.
+ * SX starts on a 16-byte boundary (else CG_ERR_INVALID_ARG), here and in cg_sketch_dense. */
 CG_API cg_status cg_sketch_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
                         const float *vals, int64_t nnz, float *SX,
                         void *ws, size_t ws_bytes, void *stream);

@@ -447,3 +447,25 @@ def test_plain_in_tiles_of_rows(n, d, m, seed):
     want = oracle.plain_csr(seed, n, d, m, X.row_ptr, X.col_idx, X.vals, row_offset=5)
     assert Yp.shape == (m, d)
     assert rel(Yp, want) < FP32_TOL
+
+
+@pytest.mark.parametrize("shift", [0, 4])
+@pytest.mark.parametrize("n,d,B,seed", [(3000, 7, 101, 61), (200_000, 101, 16383, 62)])
+def test_small_sketch_cleared_in_place(n, d, B, seed, shift):
+    """An SX of at most 8 MB is cleared by a zero-fill kernel that the scatter follows as a
+    programmatic dependent.  It clears exactly the B x d floats of a caller's SX (NaN
+    beforehand; B x d not a multiple of 4; the floats around them keep their NaN) and the
+    sketch equals the oracle's.  An SX not on a 16-byte boundary is refused."""
+    X = synth.csr_bernoulli(n, d, 0.02, seed)
+    rp, ci, v = dev_csr(X)
+    buf = torch.full((B * d + 8,), float("nan"), device="cuda")
+    SX = buf[shift:shift + B * d]
+    plan = cg().CountGauss(n, d, 4, B, seed)
+    plan.sketch_csr(rp, ci, v, out=SX)
+    plan.check()
+    SXo = oracle.sketch_csr(seed, n, d, B, X.row_ptr, X.col_idx, X.vals)
+    assert rel(SX.view(B, d).cpu().numpy(), SXo) < 1e-6
+    assert torch.isnan(torch.cat([buf[:shift], buf[shift + B * d:]])).all()
+    from paper_1606_05732_gb300 import _lib
+    with pytest.raises(_lib.CountGaussError):
+        plan.sketch_csr(rp, ci, v, out=buf[shift + 1:shift + 1 + B * d])
