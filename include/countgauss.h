@@ -149,7 +149,8 @@ typedef enum cg_op {
     CG_OP_CONTRACT = 6,       /* cg_contract alone */
     CG_OP_APPLY_CSR_HOST = 7, /* cg_apply_csr_host */
     CG_OP_APPLY_RIGHT_CSR = 8, /* cg_apply_right_csr */
-    CG_OP_APPLY_CSR_I64 = 9    /* cg_apply_csr_i64 */
+    CG_OP_APPLY_CSR_I64 = 9,   /* cg_apply_csr_i64 */
+    CG_OP_SKETCH_I64 = 10      /* cg_sketch_csr_i64 */
 } cg_op;
 
 /* ---- plans ---------------------------------------------------------------- */
@@ -265,6 +266,14 @@ CG_API cg_status cg_sketch_csr(cg_plan *plan, const int32_t *row_ptr, const int3
 
 CG_API cg_status cg_sketch_dense(cg_plan *plan, const float *X, int64_t ldx, float *SX,
                           void *ws, size_t ws_bytes, void *stream);
+
+/* cg_sketch_csr for int64 row offsets (as cg_apply_csr_i64): SX = S.X, or SX += S.X with
+ * CG_OPT_ACCUMULATE = 1, e.g. over row chunks of a stream, each with its CG_OPT_ROW_OFFSET.
+ * Workspace: cg_workspace_size(CG_OP_SKETCH_I64, nnz) (the status word only).  Errors as
+ * cg_apply_csr_i64, and CG_ERR_INVALID_ARG for an SX off a 16-byte boundary. */
+CG_API cg_status cg_sketch_csr_i64(cg_plan *plan, const int64_t *row_ptr, const int32_t *col_idx,
+                                   const float *vals, int64_t nnz, float *SX,
+                                   void *ws, size_t ws_bytes, void *stream);
 
 /* Y = G.SX alone (SX device, B x d).  Honours CG_OPT_PRECISION. */
 CG_API cg_status cg_contract(cg_plan *plan, const float *SX, float *Y,

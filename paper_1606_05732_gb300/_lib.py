@@ -29,6 +29,7 @@ OP_APPLY_CSR, OP_APPLY_DENSE, OP_ADJOINT_DENSE, OP_ADJOINT_CSR, OP_PLAIN_CSR, OP
 OP_APPLY_CSR_HOST = 7
 OP_APPLY_RIGHT_CSR = 8
 OP_APPLY_CSR_I64 = 9
+OP_SKETCH_I64 = 10
 OPT_HOST_CHUNK = 10
 OPT_HOST_READ = 11
 OPT_ACCUMULATE = 12
@@ -49,6 +50,7 @@ SIGNATURES = {
     "cg_apply_csr": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_right_csr": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_csr_i64": [P, P, P, P, I64, P, P, SZ, P],
+    "cg_sketch_csr_i64": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_csr_host": [P, P, P, P, I64, P, P, SZ, P],
     "cg_apply_csr_noalloc": [P, P, P, P, I64, P, P],
     "cg_apply_dense": [P, P, I64, P, P, SZ, P],

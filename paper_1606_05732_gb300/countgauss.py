@@ -237,7 +237,11 @@ class CountGauss:
 
     def nmf_anchors(self, row_ptr, col_idx, vals):
         """Algorithm 1 steps 1-3: Z = T.X and, per row of Z, the column of its max and
-        of its min (lowest index on ties).  Returns (Z, imax, imin)."""
+        of its min (lowest index on ties).  Returns (Z, imax, imin).  With int64 row_ptr
+        (2^31 nonzeros or more): cg_apply_csr_i64, then cg_row_argmax_argmin."""
+        if torch.is_tensor(row_ptr) and row_ptr.dtype == torch.int64:
+            Z = self.apply_csr(row_ptr, col_idx, vals)
+            return (Z, *row_argmax_argmin(Z))
         row_ptr = _need(row_ptr, torch.int32, "row_ptr")
         col_idx = _need(col_idx, torch.int32, "col_idx")
         vals = _need(vals, torch.float32, "vals")
@@ -264,15 +268,18 @@ class CountGauss:
     def sketch_csr(self, row_ptr, col_idx, vals, out=None, accumulate: bool = False) -> torch.Tensor:
         """SX = S.X (Section 1.1), or SX += S.X into `out` with accumulate=True: rows of X fed
         in chunks (each with its global row offset, set_row_offset) sketch into one SX, and a
-        saved SX plus the next row offset resumes the stream."""
-        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        saved SX plus the next row offset resumes the stream.  row_ptr int32, or int64 for
+        2^31 nonzeros or more (cg_sketch_csr_i64)."""
+        wide = torch.is_tensor(row_ptr) and row_ptr.dtype == torch.int64
+        row_ptr = _need(row_ptr, torch.int64 if wide else torch.int32, "row_ptr")
         col_idx = _need(col_idx, torch.int32, "col_idx")
         vals = _need(vals, torch.float32, "vals")
         dev = row_ptr.device
         nnz = col_idx.numel()
         SX = self._sketch_out(out, accumulate, dev)
-        ws = self.workspace(_lib.OP_SKETCH, nnz, dev)
-        _lib.check("cg_sketch_csr", self._lib.cg_sketch_csr(
+        op, name = (_lib.OP_SKETCH_I64, "cg_sketch_csr_i64") if wide else (_lib.OP_SKETCH, "cg_sketch_csr")
+        ws = self.workspace(op, nnz, dev)
+        _lib.check(name, getattr(self._lib, name)(
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(SX), _ptr(ws), ws.numel(), _stream(dev)))
         return SX
 

@@ -302,6 +302,8 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
             L.a_bytes = sx;
             L.b_bytes = contract_partials_bytes(p);
             break;
+        case CG_OP_SKETCH_I64:
+            break;
         case CG_OP_APPLY_RIGHT_CSR:
             L.a_bytes = sx;
             L.b_bytes = contract_partials_bytes(p);
@@ -635,7 +637,7 @@ cg_status cg_plan_get_option(const cg_plan *p, int32_t option, int64_t *value) {
 }
 
 cg_status cg_workspace_size(const cg_plan *p, int32_t op, int64_t nnz, size_t *bytes) {
-    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_APPLY_CSR_I64) return CG_ERR_INVALID_ARG;
+    if (p == nullptr || bytes == nullptr || op < CG_OP_APPLY_CSR || op > CG_OP_SKETCH_I64) return CG_ERR_INVALID_ARG;
     *bytes = layout_for(*p, op, nnz).total;
     return CG_OK;
 }
@@ -706,28 +708,51 @@ cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_id
     return run_contract(p, SX, Y, ws, L, st);
 }
 
+// Host-side checks of a CSR matrix with int64 row offsets and of the options its
+// scatter honours: the one-pass atomic scatter only (the deterministic, deferred and
+// partitioned scatters index with 32-bit offsets).
+cg_status check_csr_i64(const cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
+                        int64_t nnz) {
+    if (nnz < 0 || nnz > kMaxNnz64 || row_ptr == nullptr) return CG_ERR_INVALID_ARG;
+    if (nnz > 0 && (col_idx == nullptr || vals == nullptr)) return CG_ERR_INVALID_ARG;
+    if (misaligned(row_ptr, 8) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
+    if (p->deterministic || p->scatter == 2 || p->scatter == 3) return CG_ERR_UNSUPPORTED;
+    return CG_OK;
+}
+
+// SX = S.X, or with clear = false SX += S.X, for int64 row offsets.
+cg_status run_sketch_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
+                             int64_t nnz, float *SX, void *ws, cudaStream_t st, bool clear) {
+    return from_cuda(launch_sketch_csr_atomic_i64(
+        reinterpret_cast<const long long *>(row_ptr), col_idx, vals, static_cast<int>(p->n), p->d,
+        static_cast<uint32_t>(p->B), static_cast<long long>(nnz), make_key(p->seed), p->row_offset, SX, status_word(ws),
+        static_cast<int>(p->sketch_ctas), p->scatter_passes, one_pass_rows(*p, nnz), timing_pair(p, CG_KERNEL_SKETCH),
+        st, clear));
+}
+
 cg_status cg_apply_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
                            int64_t nnz, float *Y, void *ws, size_t ws_bytes, void *stream) {
     cg::NvtxRange nvtx_range("cg_apply_csr_i64");
     if (p == nullptr || Y == nullptr || misaligned(Y, 4)) return CG_ERR_INVALID_ARG;
-    if (nnz < 0 || nnz > kMaxNnz64 || row_ptr == nullptr) return CG_ERR_INVALID_ARG;
-    if (nnz > 0 && (col_idx == nullptr || vals == nullptr)) return CG_ERR_INVALID_ARG;
-    if (misaligned(row_ptr, 8) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
-    // one-pass atomic scatter only: the deterministic, deferred and partitioned scatters
-    // index with 32-bit offsets
-    if (p->deterministic || p->scatter == 2 || p->scatter == 3) return CG_ERR_UNSUPPORTED;
-    cg_status s;
+    cg_status s = check_csr_i64(p, row_ptr, col_idx, vals, nnz);
+    if (s != CG_OK) return s;
     Layout L;
     if ((s = check_ws(p, CG_OP_APPLY_CSR_I64, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
     float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
     cudaStream_t st = as_stream(stream);
-    s = from_cuda(launch_sketch_csr_atomic_i64(
-        reinterpret_cast<const long long *>(row_ptr), col_idx, vals, static_cast<int>(p->n), p->d,
-        static_cast<uint32_t>(p->B), static_cast<long long>(nnz), make_key(p->seed), p->row_offset, SX, status_word(ws),
-        static_cast<int>(p->sketch_ctas), p->scatter_passes, one_pass_rows(*p, nnz), timing_pair(p, CG_KERNEL_SKETCH),
-        st));
-    if (s != CG_OK) return s;
+    if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, st, true)) != CG_OK) return s;
     return run_contract(p, SX, Y, ws, L, st);
+}
+
+cg_status cg_sketch_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
+                            int64_t nnz, float *SX, void *ws, size_t ws_bytes, void *stream) {
+    cg::NvtxRange nvtx_range("cg_sketch_csr_i64");
+    if (p == nullptr || SX == nullptr || misaligned(SX, 16)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr_i64(p, row_ptr, col_idx, vals, nnz);
+    if (s != CG_OK) return s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_SKETCH_I64, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    return run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, as_stream(stream), !p->accumulate);
 }
 
 cg_status cg_apply_right_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,

@@ -84,7 +84,7 @@ def test_options_and_workspace(lib):
         for x in bad:
             assert lib.cg_plan_set_option(h, opt, x) == 1
     sz = ctypes.c_size_t()
-    for op in range(10):
+    for op in range(11):
         assert lib.cg_workspace_size(h, op, 1000, ctypes.byref(sz)) == 0
         assert sz.value >= 256 and sz.value % 256 == 0
     assert lib.cg_workspace_size(h, 42, 0, ctypes.byref(sz)) == 1
@@ -130,6 +130,7 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
     st, h = _plan(lib)
     P = ctypes.c_void_p
     fake = P(1 << 20)
+    sz = ctypes.c_size_t()
     assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3  # workspace too small
     assert lib.cg_apply_csr_i64(h, fake, fake, fake, -1, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_csr_i64(h, fake, fake, fake, (1 << 40) + 1, fake, fake, 1 << 30, P(0)) == 1
@@ -142,6 +143,15 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
         assert lib.cg_plan_set_option(h, opt, val) == 0
         assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
         assert lib.cg_plan_set_option(h, opt, 0) == 0
+    # the sketch alone: SX on a 16-byte boundary, the same option limits, a status word
+    assert lib.cg_sketch_csr_i64(h, fake, fake, fake, 10, P((1 << 20) + 4), fake, 1 << 30, P(0)) == 1
+    assert lib.cg_sketch_csr_i64(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
+    assert lib.cg_sketch_csr_i64(h, fake, fake, fake, -2, fake, fake, 1 << 30, P(0)) == 1
+    assert lib.cg_sketch_csr_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
+    assert lib.cg_plan_set_option(h, 2, 1) == 0
+    assert lib.cg_sketch_csr_i64(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
+    assert lib.cg_plan_set_option(h, 2, 0) == 0
+    assert lib.cg_workspace_size(h, 10, 1 << 35, ctypes.byref(sz)) == 0 and sz.value == 256
     # the adjoint at the stored entries: nnz range, null / misaligned pointers
     assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, -1, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, (1 << 40) + 1, fake, fake, 1 << 30, P(0)) == 1
@@ -151,7 +161,7 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
     assert lib.cg_apply_adjoint_i64(h, P(0), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
     # workspace: SX and the split-K partials, no scatter scratch, whatever nnz
-    sz, sz2 = ctypes.c_size_t(), ctypes.c_size_t()
+    sz2 = ctypes.c_size_t()
     assert lib.cg_workspace_size(h, 9, 10, ctypes.byref(sz)) == 0
     assert lib.cg_workspace_size(h, 9, 1 << 33, ctypes.byref(sz2)) == 0
     assert sz.value == sz2.value >= 256 + 16 * 4 * 4

@@ -198,3 +198,40 @@ def test_adjoint_past_2_pow_31_nonzeros_matches_row_blocks():
         part.check()
         assert torch.equal(dXv[k0:k1], blk)
         del blk
+
+
+def test_sketch_alone_and_streamed_in_row_chunks():
+    """cg_sketch_csr_i64: SX = S.X equals the oracle's; fed as row chunks (each chunk's
+    offsets from 0, its global row offset set, accumulating) it gives the same SX."""
+    n, d, B, seed = 90_001, 24, 4096, 46
+    X = synth.csr_ragged(n, d, seed=seed, max_row=8)
+    rp, ci, v = dev_csr64(X)
+    SXo = oracle.sketch_csr(seed, n, d, B, X.row_ptr, X.col_idx, X.vals)
+    plan = cg().CountGauss(n, d, 4, B, seed)
+    SX = plan.sketch_csr(rp, ci, v)
+    plan.check()
+    assert rel(SX.cpu().numpy(), SXo) < 1e-6
+    cuts = [0, 1, 30_000, 30_001, 77_777, n]
+    acc = torch.full((B, d), float("nan"), device="cuda")
+    for c, (r0, r1) in enumerate(zip(cuts[:-1], cuts[1:])):
+        k0, k1 = int(X.row_ptr[r0]), int(X.row_ptr[r1])
+        part = cg().CountGauss(r1 - r0, d, 4, B, seed, row_offset=r0)
+        part.sketch_csr(rp[r0:r1 + 1] - k0, ci[k0:k1], v[k0:k1], out=acc, accumulate=c > 0)
+        part.check()
+    assert rel(acc.cpu().numpy(), SXo) < 1e-6
+
+
+def test_nmf_anchors_with_wide_offsets():
+    """Algorithm 1 steps 1-3 with int64 offsets: Z as with int32 offsets, and imax / imin
+    the columns of each row's max / min of that Z, lowest index on ties."""
+    n, d, m, B, seed = 40_000, 50, 16, 2048, 47
+    X = synth.csr_bernoulli(n, d, 0.05, seed, values="uniform")
+    rp, ci, v = dev_csr64(X)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    Z, imax, imin = plan.nmf_anchors(rp, ci, v)
+    Z32, _, _ = plan.nmf_anchors(rp.int(), ci, v)
+    plan.check()
+    assert rel(Z.cpu().numpy(), Z32.cpu().numpy()) < FP32_TOL
+    Zc = Z.cpu()
+    assert torch.equal(imax.cpu().long(), torch.argmax(Zc, dim=1))
+    assert torch.equal(imin.cpu().long(), torch.argmin(Zc, dim=1))
