@@ -4,6 +4,8 @@ host before launching anything."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -188,3 +190,18 @@ def test_status_strings(lib):
     for code in range(8):
         s = lib.cg_status_string(code).decode()
         assert s.startswith("CG_")
+
+
+def test_c_program_uses_the_abi(lib, tmp_path):
+    """A C99 program (tests/abi_smoke.c) compiles against include/countgauss.h with
+    warnings as errors, links libcountgauss.so and runs its host-side calls."""
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    exe = tmp_path / "abi_smoke"
+    so_dir, so_name = os.path.split(_lib.library_path())
+    assert so_name.startswith("lib") and so_name.endswith(".so")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "abi_smoke.c"), "-L", so_dir, "-l" + so_name[3:-3],
+                    "-Wl,-rpath," + so_dir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
