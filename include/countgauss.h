@@ -33,7 +33,8 @@
  *   - CSR X: row_ptr int32[n+1] with row_ptr[0] = 0 and row_ptr[n] = nnz,
  *     col_idx int32[nnz] in [0, d) (any order within a row; duplicates are summed),
  *     vals fp32[nnz].  nnz <= 2^31 - 2^20 (the margin keeps the kernels' 32-bit
- *     indices from overflowing as they step past the last entry).
+ *     indices from overflowing as they step past the last entry).  The *_i64 entry
+ *     points take row_ptr int64[n+1] instead, for up to 2^40 entries.
  *   - ws is a device workspace of at least cg_workspace_size() bytes, 256-byte
  *     aligned.  Its first 256 bytes hold a device status word that the kernels set
  *     when a bounds check fails (the offending element is skipped, never accessed)
