@@ -36,3 +36,20 @@ def test_reference_arm_prints_one_contract_line():
 def test_reference_arm_other_ranks_print_nothing():
     env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT="29511")
     assert _run("--gpus", "2", env=env) == []
+
+
+def test_clock_record_names_the_throttle_reasons():
+    """The clocks record: NVML's event-reason bits mapped to names, median SM clock under
+    load, and the error itself in place of reasons where NVML cannot be opened."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(None)
+    c.samples, c.max_mhz = [2070.0, 1995.0, 2070.0], 2070.0
+    c.reasons = 0x4 | 0x40
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap", "hw_thermal_slowdown"]
+    c.reasons = 0
+    assert c.summary()["reasons"] == []
+    c.error = "nvml unavailable: test"
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable: test"]}
