@@ -370,7 +370,7 @@ def test_sketched_least_squares_gradient():
     r64 = Xn.astype(np.float64) @ wn.astype(np.float64) - bn.astype(np.float64)
     Tr = oracle.apply_dense(seed, m, B, r64)
     g = Xn.astype(np.float64).T @ oracle.adjoint_dense(seed, n, m, B, Tr)
-    assert abs(float(loss) - 0.5 * float(np.sum(Tr ** 2))) < 1e-4 * 0.5 * float(np.sum(Tr ** 2))
+    assert abs(float(loss.detach()) - 0.5 * float(np.sum(Tr ** 2))) < 1e-4 * 0.5 * float(np.sum(Tr ** 2))
     assert rel(w.grad.cpu().numpy(), g) < 1e-4  # X w - b in fp32 (torch) dominates
 
 
