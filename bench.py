@@ -20,6 +20,9 @@ Printed JSON line (rank 0):
                  every step, through the same public call; copied_ms and direct_ms time
                  the chunked copies and the scatter reading host memory in place
   cpu_baseline   the FP64 oracle on this machine's host cores (rank 0, N = 1)
+  rows           (N = 1) the other workloads, each a row of its own: the precision
+                 ladder, dense forward and adjoint, the 96-instance batch, the small
+                 case's latency, the SVM projection, and int64 row offsets (--rows)
 
 --impl reference times that oracle instead (the reference arm).
 """
