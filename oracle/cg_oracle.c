@@ -71,7 +71,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* The four words for (seed, idx, tag) under the project's stream layout. */
+/* The four words for (seed, idx, tag) under the project's stream layout (all randomness
+ * is a function of a short seed, as Section 4 allows). */
 static void orc_words(uint64_t seed, uint64_t idx, uint32_t tag, uint32_t out[4])
 {
     uint32_t ctr[4], key[2];
@@ -121,7 +122,8 @@ double orc_uniform24(uint32_t w)
     return (double)(2u * (w >> 9) + 1u) * (1.0 / 16777216.0);
 }
 
-/* Box-Muller: the four unit-variance normals of one Philox call. */
+/* Box-Muller (Box and Muller, 1958): the four unit-variance normals of one Philox
+ * call, the N(0,1) entries Theorem 1 asks of G and G~. */
 static void orc_box_muller4(const uint32_t w[4], double z[4])
 {
     double u0 = orc_uniform24(w[0]), u1 = orc_uniform24(w[1]);
@@ -141,7 +143,8 @@ void orc_box_muller_words(const uint32_t *w, int64_t count, double *z)
         orc_box_muller4(w + 4 * t, z + 4 * t);
 }
 
-/* One entry (r, c) of the R x C Gaussian matrix with tag `tag`. */
+/* One entry (r, c) of the R x C Gaussian matrix with tag `tag` (G: Section 2,
+ * Theorem 1; G~: Abstract). */
 static double orc_gauss_entry(uint64_t seed, uint32_t tag, int64_t R, int64_t r, int64_t c)
 {
     uint32_t w[4];
@@ -197,7 +200,7 @@ void orc_sketch_csr(uint64_t seed, int64_t n, int64_t d, int64_t B, int64_t row_
     }
 }
 
-/* S.X for dense row-major X (n x d). */
+/* S.X for dense row-major X (n x d) (Section 1.1). */
 void orc_sketch_dense(uint64_t seed, int64_t n, int64_t d, int64_t B, int64_t row_offset,
                       const double *X, double *SX)
 {
@@ -239,7 +242,7 @@ void orc_apply_csr(uint64_t seed, int64_t n, int64_t d, int64_t m, int64_t B, in
     orc_contract(seed, m, B, d, SX, Y);
 }
 
-/* T.X for dense X. */
+/* T.X = G.(S.X) for dense X (Section 1.1; Algorithm 1 steps 1-2). */
 void orc_apply_dense(uint64_t seed, int64_t n, int64_t d, int64_t m, int64_t B, int64_t row_offset,
                      const double *X, double *SX, double *Y)
 {
@@ -312,7 +315,7 @@ void orc_plain_csr(uint64_t seed, int64_t n, int64_t d, int64_t m, int64_t row_o
     }
 }
 
-/* Plain product for dense X, all m rows. */
+/* Plain product G~.X for dense X, all m rows (Abstract; Section 4). */
 void orc_plain_dense(uint64_t seed, int64_t n, int64_t d, int64_t m, int64_t row_offset,
                      const double *X, double *Y)
 {
