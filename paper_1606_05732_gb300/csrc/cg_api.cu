@@ -1,5 +1,6 @@
-// cg_api.cu -- the C ABI of libcountgauss (declared in include/countgauss.h):
-// plans, argument validation, workspace layout and dispatch to the kernels.
+// cg_api.cu -- the C ABI of libcountgauss (declared in include/countgauss.h, where each
+// entry point cites the passage of the paper it follows): plans, argument validation,
+// workspace layout and dispatch to the kernels.
 // Everything here is host code except the three generator-dump kernels.
 #include <new>
 #include <vector>

@@ -1,5 +1,6 @@
 // cg_batch.cu -- many CountGauss instances of uneven n, d, m and B (each with its own
-// seed, CSR input and output) in one persistent launch.
+// seed, CSR input and output) in one persistent launch; each instance is the transform
+// T.X = G.(S.X) of Section 1.1 (Algorithm 1 steps 1-2).
 //
 // Work items live in a queue in device memory and are claimed in order with one
 // atomic per claim by persistent CTAs:

@@ -1,6 +1,8 @@
 // cg_ffma.cuh -- the FP32 FFMA contraction of one output block over a range of K
 // slabs (G generated tile by tile in shared memory, never stored), shared by the
-// split-K contraction kernel and the batched persistent kernel.
+// split-K contraction kernel and the batched persistent kernel.  It computes the
+// second factor of T.X = G.(S.X): Y = G.SX with G the m x B matrix of i.i.d. N(0,1)
+// entries (Section 2, Theorem 1; Algorithm 1 step 2).
 #pragma once
 #include "cg_internal.cuh"
 
