@@ -57,7 +57,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--scatter", choices=["auto", "atomic", "partition", "deferred"], default="auto")
+    ap.add_argument("--scatter", choices=["auto", "atomic", "partition", "deferred", "binned"], default="auto")
     ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3", "fp8", "fp8x3"], default="fp32",
                     help="arithmetic of the Gaussian contraction in the timed step (the scatter is fp32)")
     ap.add_argument("--scatter-passes", type=int, default=0, help="bucket-range passes of the scatter (0: automatic)")

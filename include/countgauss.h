@@ -97,12 +97,16 @@ typedef enum cg_option {
     CG_OPT_TIMING = 6,        /* 1: record CUDA events around each main kernel launch
                                  (read with cg_plan_timing); 0 (default): off */
     CG_OPT_SCATTER = 7,       /* CSR scatter algorithm (atomic mode): 0 = automatic (default: 3
-                                 when SX is larger than 60 % of the L2, else 1), 1 = one L2
-                                 reduction per nonzero, 2 = partition the nonzeros by bucket
-                                 range and accumulate each range in shared memory, 3 = reduce
-                                 the rows of buckets below B/2 at once and write the others as
-                                 records reduced by a second pass (each half of SX in L2 in
-                                 turn; workspace + 8 bytes per nonzero; needs B d < 2^32) */
+                                 when SX is larger than 60 % of the L2, else 1),
+                                 1 = one L2 reduction per nonzero, 2 = partition the nonzeros by
+                                 bucket range and accumulate each range in shared memory, 3 =
+                                 reduce the rows of buckets below B/2 at once and write the
+                                 others as records reduced by a second pass (each half of SX in
+                                 L2 in turn; workspace + 8 bytes per nonzero; needs B d < 2^32),
+                                 4 = bin the nonzeros by slices of buckets (a power of two,
+                                 at most 32768 / d) into 6-byte records and sum each slice in
+                                 shared memory (workspace about 14 bytes per nonzero; needs
+                                 d <= 32768 and at most 2048 slices) */
     CG_OPT_SCATTER_PASSES = 8, /* bucket-range passes of the atomic CSR scatter (each pass streams
                                  the CSR and reduces the rows of one range of buckets, keeping
                                  that range of SX in L2); 0 = automatic (one pass), 1..16 forced */
@@ -202,7 +206,7 @@ CG_API cg_status cg_apply_csr(cg_plan *plan, const int32_t *row_ptr, const int32
  * first nonzero.  Y (device, m x d) is overwritten.  Workspace:
  * cg_workspace_size(CG_OP_APPLY_CSR_I64, nnz).  Errors: CG_ERR_INVALID_ARG for null or
  * misaligned pointers or nnz out of range; CG_ERR_UNSUPPORTED with CG_OPT_DETERMINISTIC
- * = 1 or CG_OPT_SCATTER 2 or 3.  Out-of-range column indices, out-of-range or decreasing
+ * = 1 or CG_OPT_SCATTER 2, 3 or 4.  Out-of-range column indices, out-of-range or decreasing
  * row offsets, and a chunk of rows (at most 128 consecutive rows) holding more than
  * 2^31 - 2^20 stored entries are reported through the status word, the entries concerned
  * skipped. */

@@ -23,7 +23,7 @@ STATUS_NAMES = {
 PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3, "fp8x3": 4}
 OPT_PRECISION, OPT_DETERMINISTIC, OPT_ROW_OFFSET, OPT_KSPLIT, OPT_SKETCH_CTAS, OPT_TIMING = 1, 2, 3, 4, 5, 6
 OPT_SCATTER, OPT_SCATTER_PASSES, OPT_SCATTER_ROWS = 7, 8, 9
-SCATTER = {"auto": 0, "atomic": 1, "partition": 2, "deferred": 3}
+SCATTER = {"auto": 0, "atomic": 1, "partition": 2, "deferred": 3, "binned": 4}
 KERNEL_SKETCH, KERNEL_CONTRACT, KERNEL_PLAIN, KERNEL_ADJOINT_W, KERNEL_GATHER = range(5)
 OP_APPLY_CSR, OP_APPLY_DENSE, OP_ADJOINT_DENSE, OP_ADJOINT_CSR, OP_PLAIN_CSR, OP_SKETCH, OP_CONTRACT = range(7)
 OP_APPLY_CSR_HOST = 7

@@ -218,16 +218,29 @@ bool use_partition(const cg_plan &p) {
     return p.scatter == 2 && partition_supported(p);
 }
 
-// Whether a CSR scatter through plan p defers half of SX to a second pass: on request
-// (CG_OPT_SCATTER = 3), or automatically when SX is larger than 60 % of the L2, where
-// random reductions into it start to miss (and bucket-range passes are not forced).
-bool use_deferred(const cg_plan &p) {
-    if (p.deterministic || use_partition(p) || !deferred_supported(p.B, p.d)) return false;
-    if (p.scatter == 3) return true;
-    if (p.scatter != 0 || p.scatter_passes > 0) return false;
+// Whether SX is larger than 60 % of the L2, where random reductions into it start to miss.
+bool sx_past_l2(const cg_plan &p) {
     const double sx = static_cast<double>(p.B) * p.d * sizeof(float);
     const int l2 = l2_bytes();
     return l2 > 0 && sx > 0.6 * l2;
+}
+
+// Whether a CSR scatter through plan p bins the nonzeros by bucket slice and sums each
+// slice in shared memory: on request (CG_OPT_SCATTER = 4) only; on GB300 at the largest
+// workload it measures slightly slower than the deferred scatter (0.98 against 0.93 ms).
+bool use_binned(const cg_plan &p, int64_t nnz) {
+    (void)nnz;
+    return !p.deterministic && p.scatter == 4 && binned_supported(p.n, p.d, p.B);
+}
+
+// Whether a CSR scatter through plan p defers half of SX to a second pass: on request
+// (CG_OPT_SCATTER = 3), or automatically for an SX past the L2 (and bucket-range passes
+// not forced).
+bool use_deferred(const cg_plan &p, int64_t nnz) {
+    if (p.deterministic || use_partition(p) || use_binned(p, nnz) || !deferred_supported(p.B, p.d)) return false;
+    if (p.scatter == 3) return true;
+    if (p.scatter != 0 || p.scatter_passes > 0) return false;
+    return sx_past_l2(p);
 }
 
 // Scratch bytes of the CSR scatter through plan p (region C).
@@ -237,7 +250,9 @@ size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
         *part = partition_layout(p, nnz);
         return part->bytes;
     }
-    if (use_deferred(p)) return sketch_deferred_scratch_bytes(nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas)));
+    if (use_binned(p, nnz)) return sketch_binned_scratch_bytes(p.n, p.d, p.B, nnz, static_cast<int>(p.sketch_ctas));
+    if (use_deferred(p, nnz))
+        return sketch_deferred_scratch_bytes(nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas)));
     return 0;
 }
 
@@ -372,15 +387,24 @@ int one_pass_rows(const cg_plan &p, int64_t nnz) {
 }
 
 // SX = S.X, or with clear = false SX += S.X (atomic and deferred scatters only).
+// host_mapped: the CSR arrays are page-locked host memory read in place (no L2 prefetch
+// of them).
 cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
-                         int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st, bool clear = true) {
+                         int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st, bool clear = true,
+                         bool host_mapped = false) {
     if (p->deterministic)
         return from_cuda(launch_sketch_csr_fixed(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                                  static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),
                                                  p->row_offset, SX, region(ws, L.c_off), status_word(ws),
                                                  static_cast<int>(p->sketch_ctas), p->scatter_rows,
                                                  timing_pair(p, CG_KERNEL_SKETCH), st));
-    if (use_deferred(*p))
+    if (use_binned(*p, nnz))
+        return from_cuda(launch_sketch_csr_binned(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
+                                                  static_cast<uint32_t>(p->B), static_cast<int>(nnz),
+                                                  make_key(p->seed), p->row_offset, SX, status_word(ws),
+                                                  region(ws, L.c_off), static_cast<int>(p->sketch_ctas),
+                                                  timing_pair(p, CG_KERNEL_SKETCH), st, clear, !host_mapped));
+    if (use_deferred(*p, nnz))
         return from_cuda(launch_sketch_csr_deferred(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                                     static_cast<uint32_t>(p->B), static_cast<int>(nnz),
                                                     make_key(p->seed), p->row_offset, SX, status_word(ws),
@@ -589,7 +613,7 @@ cg_status cg_plan_set_option(cg_plan *p, int32_t option, int64_t value) {
             p->timing = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_SCATTER:
-            if (value < 0 || value > 3) return CG_ERR_INVALID_ARG;
+            if (value < 0 || value > 4) return CG_ERR_INVALID_ARG;
             p->scatter = static_cast<int32_t>(value);
             return CG_OK;
         case CG_OPT_SCATTER_PASSES:
@@ -717,7 +741,7 @@ cg_status check_csr_i64(const cg_plan *p, const int64_t *row_ptr, const int32_t 
     if (nnz < 0 || nnz > kMaxNnz64 || row_ptr == nullptr) return CG_ERR_INVALID_ARG;
     if (nnz > 0 && (col_idx == nullptr || vals == nullptr)) return CG_ERR_INVALID_ARG;
     if (misaligned(row_ptr, 8) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
-    if (p->deterministic || p->scatter == 2 || p->scatter == 3) return CG_ERR_UNSUPPORTED;
+    if (p->deterministic || p->scatter == 2 || p->scatter == 3 || p->scatter == 4) return CG_ERR_UNSUPPORTED;
     return CG_OK;
 }
 
@@ -896,7 +920,7 @@ cg_status cg_apply_csr_host(cg_plan *p, const int32_t *row_ptr, const int32_t *c
     const float *dv = nullptr;
     if (host_read_direct(*p, row_ptr, col_idx, vals, nnz, &drp, &dci, &dv)) {
         // the kernels stream the host arrays in place (offsets checked on the device)
-        if ((s = run_sketch_csr(p, drp, dci, dv, nnz, SX, ws, Lrest, st)) != CG_OK) return s;
+        if ((s = run_sketch_csr(p, drp, dci, dv, nnz, SX, ws, Lrest, st, true, true)) != CG_OK) return s;
         if ((s = run_contract(p, SX, Yd, ws, L, st)) != CG_OK) return s;
         return from_cuda(cudaMemcpyAsync(Y, Yd, static_cast<size_t>(p->m) * p->d * sizeof(float),
                                          cudaMemcpyDeviceToHost, st));

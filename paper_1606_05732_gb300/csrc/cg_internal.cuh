@@ -145,6 +145,16 @@ cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, c
                                        void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
                                        bool clear = true);
 
+// ---- binned scatter (cg_sketch_bin.cu) -----------------------------------------
+// Nonzeros binned by bucket range (slices of SX that fit in shared memory), each slice
+// summed in shared memory and written once (for an SX larger than the L2 holds).
+bool binned_supported(int64_t n, int d, int64_t B);
+size_t sketch_binned_scratch_bytes(int64_t n, int d, int64_t B, int64_t nnz, int ctas);
+cudaError_t launch_sketch_csr_binned(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                     void *scratch, int ctas, const EventPair *ev, cudaStream_t stream,
+                                     bool clear = true, bool prefetch = true);
+
 // Bytes of the L2 of the current device (cached per device; 0 without a device).
 int l2_bytes();
 

@@ -140,8 +140,8 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
     assert lib.cg_apply_csr_i64(h, P((1 << 20) + 4), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1  # 4-aligned
     assert lib.cg_apply_csr_i64(h, fake, P(0), fake, 10, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
-    # the deterministic, deferred and partitioned scatters take 32-bit offsets only
-    for opt, val in ((2, 1), (7, 3), (7, 2)):
+    # the deterministic, deferred, partitioned and binned scatters take 32-bit offsets only
+    for opt, val in ((2, 1), (7, 3), (7, 2), (7, 4)):
         assert lib.cg_plan_set_option(h, opt, val) == 0
         assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
         assert lib.cg_plan_set_option(h, opt, 0) == 0

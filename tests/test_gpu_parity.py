@@ -108,7 +108,7 @@ def make_input(n, d, seed, kind):
     return synth.csr_bernoulli(n, d, p, seed=seed, values="uniform" if kind.endswith("u") else "normal")
 
 
-@pytest.mark.parametrize("scatter", ["atomic", "partition", "deferred"])
+@pytest.mark.parametrize("scatter", ["atomic", "partition", "deferred", "binned"])
 @pytest.mark.parametrize("n,d,m,B,seed,kind", CASES)
 def test_apply_csr_parity(n, d, m, B, seed, kind, scatter):
     X = make_input(n, d, seed, kind)
@@ -226,6 +226,73 @@ def test_deferred_scatter_edges(rows):
     with pytest.raises(_lib.CountGaussError):
         plan.check()
     plan.check()
+
+
+@pytest.mark.parametrize("n,d,B,kind", [(70001, 37, 3001, "ragged"),      # one tile per lane row, ragged ends
+                                         (300_000, 128, 4096, "bern0.01"),  # the ladder's density, 16 slices
+                                         (40_000, 64, 100_000, "bern0.05"),  # 196 slices, 3.2 nonzeros per row
+                                         (5000, 1, 1 << 20, "bern0.3")])    # d = 1, 32 slices
+def test_binned_scatter_edges(n, d, B, kind):
+    """The binned scatter (records sorted by bucket slice, each slice summed in shared
+    memory): many tiles per CTA with ragged ends, empty rows, a row offset (shard), and the
+    error report for a bad column index and for out-of-order offsets, skipped like the
+    one-pass scatter does."""
+    from paper_1606_05732_gb300 import _lib
+    m, seed = 13, 21
+    X = make_input(n, d, 5, kind) if kind != "ragged" else synth.csr_ragged(n, d, seed=5, max_row=6)
+    rp, ci, v = dev_csr(X)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="binned", row_offset=12345)
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=12345, return_sx=True)
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL
+    bad_ci = ci.clone()
+    bad_ci[X.nnz // 2] = d + 3
+    SXb = plan.sketch_csr(rp, bad_ci, v).cpu().numpy()
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    # the bad entry is skipped: the rest of the sketch is unchanged
+    k = X.nnz // 2
+    i = int(np.searchsorted(X.row_ptr, k, side="right") - 1)
+    h, s = oracle.hash_sign(seed, B, 12345 + i, 1)
+    SXo2 = SXo.copy()
+    SXo2[h[0], X.col_idx[k]] -= s[0] * X.vals[k]
+    assert rel(SXb, SXo2) < 1e-6
+    bad_rp = rp.clone()
+    bad_rp[n // 2], bad_rp[n // 2 + 1] = rp[n // 2 + 1].item() + 1, rp[n // 2].item()
+    plan.sketch_csr(bad_rp, ci, v)
+    with pytest.raises(_lib.CountGaussError):
+        plan.check()
+    plan.check()
+
+
+def test_binned_overflow_and_long_tiles():
+    """Full rows of 4096 entries: a row's records all land in one slice (8 buckets of 4096
+    columns), far past that slice's share of its CTA's region, so they spill to the overflow
+    list; a tile of rows holds far more records than the shared staging buffer, so most go
+    straight to the regions.  Neither may change the result."""
+    n, d, m, B, seed = 256, 4096, 8, 512, 9
+    X = synth.csr_bernoulli(n, d, 1.0, seed=3)
+    rp, ci, v = dev_csr(X)
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="binned")
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL
+    # one row holding a quarter of a sparse matrix's entries
+    n, d, B = 20000, 512, 1 << 14
+    Xs = synth.csr_bernoulli(n, d, 0.01, seed=4).to_dense()
+    Xs[777, :] = np.random.default_rng(1).standard_normal(d).astype(np.float32)
+    X = synth.csr_from_dense(Xs)
+    rp, ci, v = dev_csr(X)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="binned")
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    assert rel(SX, oracle.sketch_csr(seed, n, d, B, X.row_ptr, X.col_idx, X.vals)) < 1e-6
 
 
 def test_partition_overflow_path():

@@ -30,7 +30,7 @@ def chunk(X, a, b):
             torch.from_numpy(X.vals[k0:k1].astype(np.float32)).cuda())
 
 
-@pytest.mark.parametrize("scatter", ["atomic", "deferred"])
+@pytest.mark.parametrize("scatter", ["atomic", "deferred", "binned"])
 def test_streamed_chunks_and_resume(scatter):
     n, d, m, B, seed = 30011, 24, 16, 2048, 31
     X = synth.csr_bernoulli(n, d, 0.05, seed=seed)
