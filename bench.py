@@ -1,28 +1,33 @@
 #!/usr/bin/env python
 """Throughput of the CountGauss transform T.X = G.(S.X) on GB300.
 
-One step = one cg_apply_csr call on the large NMF-like workload (n = 2^24 rows,
-d = 64, Bernoulli density 0.05, U[0,1) values, m = 32, B = 2^17, seed 2): the
-CountSketch scatter, the in-kernel Gaussian contraction and its split-K sum.
-Inputs are resident in HBM when the timed region starts; the CSR arrays (~500 MB)
-exceed L2, so no flush is needed between steps.
+One step = one cg_apply_csr call on the largest workload, the precision ladder's input
+(n = 2^26 rows, d = 128, Bernoulli density 0.01, N(0,1) values, m = 128, B = 2^18,
+seed 3), in FP32: the CountSketch scatter, the in-kernel Gaussian contraction and its
+split-K sum.  Inputs are resident in HBM when the timed region starts; the CSR arrays
+(~956 MB) exceed L2, so no flush is needed between steps.
 
 Printed JSON line (rank 0):
   value          nnz(X)/s over all ranks (weak scaling: every rank sketches its own
                  shard of n rows, global row offset rank*n; the m x d outputs are
-                 summed across ranks each step)
-  roofline       the scatter kernel (dominant): algorithmic bytes per launch
-                 (8 nnz + 4 (n+1) + 4 B d) over its CUDA-event duration, against the
-                 measured HBM copy bandwidth
+                 summed across ranks each step).  The timed loop records no per-kernel
+                 events; the stage times come from a second loop of the same steps
+                 (stage_pass)
+  roofline       the scatter (dominant; at this size the deferred pair of kernels):
+                 algorithmic bytes per launch (8 nnz + 4 (n+1) + 4 B d) over its
+                 CUDA-event duration in the stage pass, against the measured HBM copy
+                 bandwidth; traffic from one ncu capture of the same launch
   plain          the plain G~.X on the same input and GPU, and the speedup over it
   e2e            the same metric through cg_apply_csr_host: the CSR in pinned host memory
                  copied host->device in chunks that overlap the scatter, Y read back
                  every step, through the same public call; copied_ms and direct_ms time
                  the chunked copies and the scatter reading host memory in place
-  cpu_baseline   the FP64 oracle on this machine's host cores (rank 0, N = 1)
-  rows           (N = 1) the other workloads, each a row of its own: the precision
-                 ladder, dense forward and adjoint, the 96-instance batch, the small
-                 case's latency, the SVM projection, and int64 row offsets (--rows)
+  cpu_baseline   the FP64 oracle on this machine's host cores (rank 0, N = 1): all cores
+                 (row shards and ranges of G's columns in host threads) and one core
+  rows           (N = 1) the other workloads, each a row of its own: the NMF-like input
+                 (n = 2^24, d = 64), the precision ladder, dense forward and adjoint, the
+                 96-instance batch, the small case's latency, the SVM projection, and
+                 int64 row offsets (--rows)
 
 --impl reference times that oracle instead (the reference arm).
 """
@@ -39,7 +44,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "nmf_n16M_d64"
+WORKLOAD = "ladder_n64M_d128"
 METRIC = "CountGauss nnz(X)/s & HBM-roofline %; speedup vs plain G̃·X, same GB300"
 UNIT = "nnz/s"
 
@@ -70,8 +75,10 @@ def parse_args():
     ap.add_argument("--kl-sweep", action="store_true",
                     help="instead of the step: Theorem 1's KL / Pinsker bound and Lemma 5's distinguisher vs B")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
-    ap.add_argument("--rows", default="ladder,grad,batch,small,svm,wide",
-                    help="comma list of the other rows to measure (ladder, grad, batch, small, svm, wide)")
+    ap.add_argument("--step-only", action="store_true",
+                    help="time the step alone (no plain product, deterministic mode or host-input call): for profiling")
+    ap.add_argument("--rows", default="nmf,ladder,grad,batch,small,svm,wide",
+                    help="comma list of the other rows to measure (nmf, ladder, grad, batch, small, svm, wide)")
     return ap.parse_args()
 
 
@@ -176,45 +183,84 @@ def source_hash(*names):
 # ------------------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ------------------------------------------------------------------------------------
-def oracle_sample(workload: str, fraction: float):
-    from paper_1606_05732_gb300 import synth
-    X, w = synth.workload_csr(workload, scale_rows=fraction)
-    return X, w
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # not on Linux
+        return os.cpu_count() or 1
 
 
-def time_oracle(X, w, steps: int, warmup: int):
+def oracle_fraction_step(X, w, frac, threads):
+    """One oracle apply on a fraction `frac` of the workload: the sketch of the first
+    frac*n rows and the contraction over the first frac*B columns of G (so both stages
+    do `frac` of the whole job's work), on `threads` host threads.  Returns (seconds,
+    nonzeros of the sampled rows)."""
     import oracle
-    oracle.build()
-    times = []
-    for it in range(warmup + steps):
-        t0 = time.perf_counter()
-        oracle.apply_csr(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals)
-        dt = time.perf_counter() - t0
-        if it >= warmup:
-            times.append(dt)
-    return times
+    ns = max(1, int(X.n * frac))
+    k1 = int(X.row_ptr[ns])
+    b1 = max(1, int(w["B"] * frac))
+    t0 = time.perf_counter()
+    oracle.apply_csr_parallel(w["seed"], ns, X.d, w["m"], w["B"], X.row_ptr[:ns + 1], X.col_idx[:k1],
+                              X.vals[:k1], threads, b_range=(0, b1))
+    return time.perf_counter() - t0, k1
 
 
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    fraction = 0.25
-    X, w = oracle_sample(args.workload, fraction)
-    times = time_oracle(X, w, args.steps, args.warmup)
+    import oracle
+    oracle.build()
+    from paper_1606_05732_gb300 import synth
+    X, w = synth.workload_csr(args.workload)
+    cores = host_cores()
+    # the fraction of the workload per step: at most 1/16, and small enough that the
+    # whole run (warm-up and timed steps) takes about two minutes on these cores
+    frac = 1.0 / 64
+    dt, _ = oracle_fraction_step(X, w, frac, cores)
+    frac = min(1.0 / 16, frac * max(0.05, 120.0 / max(1, args.steps + args.warmup) / max(dt, 1e-3)))
+    times, nnzs = [], []
+    for it in range(args.warmup + args.steps):
+        dt, k1 = oracle_fraction_step(X, w, frac, cores)
+        if it >= args.warmup:
+            times.append(dt)
+            nnzs.append(k1)
     step = statistics.mean(times)
-    value = X.nnz / step
-    sample = (f"{fraction:.2f} of the rows of {args.workload} (n={X.n}, nnz={X.nnz}, m={w['m']}, B={w['B']}): "
-              f"one full oracle apply per step, single thread")
+    value = statistics.mean(nnzs) / step
+    sample = (f"per step {frac:.5f} of {args.workload} (n={X.n}, nnz={X.nnz}, m={w['m']}, B={w['B']}): the FP64 "
+              f"oracle's sketch of the first {frac:.5f} n rows and its contraction over the first {frac:.5f} B "
+              f"columns of G, on {cores} host threads (row shards, ranges of G's columns)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": X.n, "d": X.d, "nnz": X.nnz, "m": w["m"], "B": w["B"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": args.workload, "n": X.n, "d": X.d, "nnz": X.nnz, "m": w["m"], "B": w["B"],
+                   "fraction_per_step": frac},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_baselines(X, w):
+    """The FP64 oracle on this machine's host cores, the whole workload once on all cores
+    (row shards and ranges of G's columns in host threads, summed) and once on one core
+    (if that takes under about two minutes: else on a fraction of the rows and of G's
+    columns, which scales both stages alike)."""
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    t0 = time.perf_counter()
+    oracle.apply_csr_parallel(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals, cores)
+    t_all = time.perf_counter() - t0
+    est_one = t_all * cores
+    frac = 1.0 if est_one < 120 else 0.25
+    dt, k1 = oracle_fraction_step(X, w, frac, 1)
+    return {"value": X.nnz / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload (n={X.n}, nnz={X.nnz}), FP64, {cores} host threads, {t_all:.2f} s",
+            "one_core": {"value": k1 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": ("the whole workload" if frac == 1.0 else f"{frac} of the rows and of the columns of G")
+                         + f", FP64, one thread, {dt:.2f} s"}}
 
 
 # ------------------------------------------------------------------------------------
@@ -327,10 +373,13 @@ def _ladder_row(dev, reps, csr_dev, stream):
         plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"], precision=prec)
         Y = torch.empty(w["m"], w["d"], dtype=torch.float32, device=dev)
         plan.apply_csr(rp, ci, v, out=Y)
+        ms = _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, stream)
+        # the contraction kernel alone: event pairs around it, in calls of their own
         plan.enable_timing(True)
         plan.kernel_time(_lib.KERNEL_CONTRACT)
-        ms = _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, stream)
+        _time_calls(lambda: plan.apply_csr(rp, ci, v, out=Y), reps, stream, warm=0)
         cms, cn = plan.kernel_time(_lib.KERNEL_CONTRACT)
+        plan.enable_timing(False)
         plan.check()
         flops = 2.0 * w["m"] * w["B"] * w["d"]
         ladder[prec] = {"ms_per_call": ms, "nnz_per_s": X.nnz / (ms / 1e3), "contract_kernel_ms": cms / max(1, cn),
@@ -492,22 +541,32 @@ def _svm_row(dev, reps, csr_dev, stream):
                                        "input": "synthetic TechTC-shaped pair (shape stand-in, not the dataset)"}}
 
 
-def run_ours(args):
+def scatter_kernels(args, B, d, dev):
+    """Names and sources of the scatter kernels cg_apply_csr runs for this plan: the
+    deferred pair once SX exceeds 60 % of the L2 (automatic), else the one-pass kernel."""
+    import torch
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    if args.scatter == "partition":
+        return "partition_kernel+accumulate_kernel", ("cg_sketch_part.cu", "cg_rng.cuh"), 5
+    if args.scatter == "binned":
+        return "bin_pass_kernel+bin_reduce_kernel", ("cg_sketch_bin.cu", "cg_scatter.cuh", "cg_rng.cuh"), 5
+    if args.scatter == "deferred" or (args.scatter == "auto" and args.scatter_passes == 0
+                                      and 4 * B * d > 0.6 * l2 and B * d < (1 << 32)):
+        return "split_pass_kernel+replay_records_kernel", ("cg_sketch_defer.cu", "cg_scatter.cuh", "cg_rng.cuh"), 4
+    return "sketch_csr_kernel", ("cg_sketch.cu", "cg_scatter.cuh", "cg_rng.cuh"), 3
+
+
+def measure_workload(args, name, dev, rank=0, world=1, pg=None, steps=None, e2e=True, det=True, plain=True):
+    """One workload's step: cg_apply_csr timed over `steps` calls with CUDA events (no
+    per-kernel events inside), then the same calls again with per-kernel event pairs
+    (the stage pass), the plain product, the deterministic mode, and (e2e) the
+    host-input call.  Returns (record, X, workload dict)."""
     import numpy as np
     import torch
 
     from paper_1606_05732_gb300 import _lib, countgauss, synth
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
-
-    wl = dict(synth.WORKLOADS[args.workload])
+    steps = args.steps if steps is None else steps
+    wl = dict(synth.WORKLOADS[name])
     n, d, m, B, seed = wl["n"], wl["d"], wl["m"], wl["B"], wl["seed"]
     X = synth.csr_bernoulli(n, d, wl["p"], seed=seed + 7919 * rank, values=wl["values"])
     nnz = X.nnz
@@ -517,18 +576,7 @@ def run_ours(args):
     rp, ci, v = rp_h.to(dev), ci_h.to(dev), v_h.to(dev)
     plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, scatter=args.scatter, precision=args.precision,
                                  scatter_passes=args.scatter_passes, scatter_rows=args.scatter_rows)
-    partitioned = args.scatter == "partition"
-    # automatic: the deferred two-pass scatter once SX exceeds 60 % of the L2, else one pass
-    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-    deferred = args.scatter == "deferred" or (args.scatter == "auto" and args.scatter_passes == 0
-                                              and 4 * B * d > 0.6 * l2 and B * d < (1 << 32))
-    if partitioned:
-        scatter_kernel, scatter_src = "partition_kernel+accumulate_kernel", ("cg_sketch_part.cu", "cg_rng.cuh")
-    elif deferred:
-        scatter_kernel = "split_pass_kernel+replay_records_kernel"
-        scatter_src = ("cg_sketch_defer.cu", "cg_scatter.cuh", "cg_rng.cuh")
-    else:
-        scatter_kernel, scatter_src = "sketch_csr_kernel", ("cg_sketch.cu", "cg_scatter.cuh", "cg_rng.cuh")
+    kname, ksrc, launches_per_step = scatter_kernels(args, B, d, dev)
     Y = torch.empty(m, d, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -540,158 +588,154 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     plan.check()
+
+    def timed(label):
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        if pg is not None:
+            pg.barrier()
+        ms = e0.elapsed_time(e1)
+        if pg is not None:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps, clk.summary()
+
+    ms_step, clocks = timed("headline")
+    # the stage pass: the same steps with an event pair around every kernel
     plan.enable_timing(True)
     plan.kernel_time(_lib.KERNEL_SKETCH)
     plan.kernel_time(_lib.KERNEL_CONTRACT)
-
-    if pg is not None:
-        pg.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-    if pg is not None:
-        pg.barrier()
-    ms_total = e0.elapsed_time(e1)
+    stage_ms_step, _ = timed("stages")
     sketch_ms, sketch_n = plan.kernel_time(_lib.KERNEL_SKETCH)
     contract_ms, contract_n = plan.kernel_time(_lib.KERNEL_CONTRACT)
     plan.enable_timing(False)
     plan.check()
-    if pg is not None:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
     value = world * nnz / (ms_step / 1e3)
 
-    # roofline of the scatter kernel
     peak, peak_kind = measured_peaks()
     alg_bytes = 8 * nnz + 4 * (n + 1) + 4 * B * d
     sketch_avg_s = (sketch_ms / max(1, sketch_n)) / 1e3
     achieved = alg_bytes / sketch_avg_s / 1e9
-    src = source_hash(*scatter_src)
-    traffic = NCU_TRAFFIC.get((src, args.workload))
+    traffic = NCU_TRAFFIC.get((source_hash(*ksrc), name))
     red_ceiling = reduction_ceiling(dev, nnz, B * d) if rank == 0 else None
 
-    # plain G~.X on the same input
-    plain_steps = max(3, args.steps // 4)
     Yp = torch.empty_like(Y)
-    for _ in range(2):
-        plan.plain_csr(rp, ci, v, out=Yp)
-    torch.cuda.synchronize(dev)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for _ in range(plain_steps):
-        plan.plain_csr(rp, ci, v, out=Yp)
-    p1.record(stream)
-    torch.cuda.synchronize(dev)
-    plain_ms = p0.elapsed_time(p1) / plain_steps
+    plain_ms = _time_calls(lambda: plan.plain_csr(rp, ci, v, out=Yp), max(3, steps // 20), stream) if plain else None
+    rec = {
+        "workload": name, "n": n, "d": d, "p": wl["p"], "values": wl["values"], "nnz_per_rank": nnz, "m": m, "B": B,
+        "seed": seed, "ms_per_step": ms_step, "value": value, "clocks": clocks,
+        "stage_pass": {"ms_per_step": stage_ms_step, "sketch_kernel_ms": sketch_ms / max(1, sketch_n),
+                       "contract_kernel_ms": contract_ms / max(1, contract_n), "launches": sketch_n},
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sketch_avg_s * 1e3, "launches": sketch_n,
+                     "reduction_bound": None if red_ceiling is None else {
+                         "reductions_per_launch": nnz, "achieved_per_s": nnz / sketch_avg_s,
+                         "ceiling_per_s": red_ceiling["per_s"],
+                         "frac": (nnz / sketch_avg_s) / red_ceiling["per_s"], "ceiling": red_ceiling}},
+        "plain": None if plain_ms is None else {
+            "ms_per_step": plain_ms, "value": world * nnz / (plain_ms / 1e3), "unit": UNIT,
+            "speedup_countgauss_over_plain": plain_ms / ms_step},
+        "gpu_launches_per_step": launches_per_step,
+    }
+    if det:
+        det_plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, deterministic=True)
+        Yd = torch.empty_like(Y)
+        det_ms = _time_calls(lambda: det_plan.apply_csr(rp, ci, v, out=Yd), max(3, steps // 20), stream)
+        det_plan.check()
+        del det_plan
+        rec["deterministic"] = {"ms_per_step": det_ms, "value": world * nnz / (det_ms / 1e3), "unit": UNIT}
+    if e2e:
+        # end to end through the host-input call: H2D of the CSR, apply, D2H of Y, every step
+        # (cg_apply_csr_host: the CSR in pinned host memory is copied in chunks on a second
+        # stream while earlier chunks are scattered, or read in place by the scatter; Y comes
+        # back to host memory)
+        Y_h = torch.empty(m, d, dtype=torch.float32).pin_memory()
+        plan.set_host_chunk(args.host_chunk)
 
-    # deterministic mode (bucket-range partition + exact fixed-point sums) on the same input
-    det_plan = countgauss.CountGauss(n, d, m, B, seed, row_offset=rank * n, deterministic=True)
-    Yd = torch.empty_like(Y)
-    det_ms = _time_calls(lambda: det_plan.apply_csr(rp, ci, v, out=Yd), max(3, args.steps // 10), stream)
-    det_plan.check()
-    del det_plan
+        def e2e_step():
+            plan.apply_csr_host(rp_h, ci_h, v_h, out=Y_h, device=dev)
+            if pg is not None:
+                Y.copy_(Y_h, non_blocking=True)
+                pg.all_reduce(Y)
+                Y_h.copy_(Y, non_blocking=True)
 
-    # end to end through the host-input call: H2D of the CSR, apply, D2H of Y, every step
-    # (cg_apply_csr_host: the CSR in pinned host memory is copied in chunks on a second
-    # stream while earlier chunks are scattered, or read in place by the scatter; Y comes
-    # back to host memory)
-    Y_h = torch.empty(m, d, dtype=torch.float32).pin_memory()
-    plan.set_host_chunk(args.host_chunk)
-
-    def e2e_step():
-        plan.apply_csr_host(rp_h, ci_h, v_h, out=Y_h, device=dev)
+        e2e_steps = max(3, steps // 10)
+        e2e_ms = _time_calls(e2e_step, e2e_steps, stream)
         if pg is not None:
-            Y.copy_(Y_h, non_blocking=True)
-            pg.all_reduce(Y)
-            Y_h.copy_(Y, non_blocking=True)
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        modes = {}  # the two ways of reading the host CSR, each forced (this rank's time)
+        for mode in ("copied", "direct"):
+            plan.set_host_read(mode)
+            modes[mode + "_ms"] = _time_calls(e2e_step, e2e_steps, stream)
+        plan.set_host_read("auto")
+        h2d = int(rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 4)
+        rec["e2e"] = {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": int(m * d * 4), "ms_per_step": e2e_ms, "call": "cg_apply_csr_host",
+                      "host_read": "auto", **modes}
+    del rp, ci, v, rp_h, ci_h, v_h, plan
+    torch.cuda.empty_cache()
+    return rec, X, wl
 
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize(dev)
-    e2e_steps = max(3, args.steps // 2)
-    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    q0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    q1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = q0.elapsed_time(q1) / e2e_steps
-    if pg is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_modes = {}  # the two ways of reading the host CSR, each forced (this rank's time)
-    for mode in ("copied", "direct"):
-        plan.set_host_read(mode)
-        for _ in range(2):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        q0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        q1.record(stream)
-        torch.cuda.synchronize(dev)
-        e2e_modes[mode + "_ms"] = q0.elapsed_time(q1) / e2e_steps
-    plan.set_host_read("auto")
-    h2d = int(rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 4)
-    d2h = int(m * d * 4)
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    head, X, wl = measure_workload(args, args.workload, dev, rank, world, pg, e2e=not args.step_only,
+                                   det=not args.step_only, plain=not args.step_only)
 
     rows = None
     if rank == 0 and world == 1 and not args.no_rows:
-        torch.cuda.empty_cache()
-        rows = measure_rows(dev, max(5, args.steps // 10), tuple(args.rows.split(",")))
+        which = tuple(args.rows.split(","))
+        rows = {}
+        if "nmf" in which and args.workload != "nmf_n16M_d64":
+            rec, _, _ = measure_workload(args, "nmf_n16M_d64", dev, e2e=False)
+            rows["nmf_n16M_d64"] = rec
+        rows.update(measure_rows(dev, max(5, args.steps // 10), which))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        reps, total = 0, 0.0
-        while reps < 1 or (total < 10.0 and reps < 20):
-            t0 = time.perf_counter()
-            oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=0)
-            total += time.perf_counter() - t0
-            reps += 1
-        dt = total / reps
-        cpu = {"value": nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the full workload (n={n}, nnz={nnz}), FP64, single thread, mean of {reps} runs, "
-                         f"{dt:.2f} s each"}
+        cpu = cpu_baselines(X, wl)
 
     if rank == 0:
+        h2d = 4 * (head["n"] + 1) + 8 * head["nnz_per_rank"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else f"f32+{args.precision}",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "d": d, "p": wl["p"], "values": wl["values"],
-                       "nnz_per_rank": nnz, "m": m, "B": B, "seed": seed,
+            "config": {"workload": args.workload, "n": head["n"], "d": head["d"], "p": head["p"],
+                       "values": head["values"], "nnz_per_rank": head["nnz_per_rank"], "m": head["m"],
+                       "B": head["B"], "seed": head["seed"],
                        "l2": "CSR inputs (%.0f MB) exceed L2; no flush" % (h2d / 1e6)},
-            "roofline": {"kernel": scatter_kernel, "bound": "hbm", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sketch_avg_s * 1e3,
-                         "launches": sketch_n,
-                         "reduction_bound": None if red_ceiling is None else {
-                             "reductions_per_launch": nnz, "achieved_per_s": nnz / sketch_avg_s,
-                             "ceiling_per_s": red_ceiling["per_s"],
-                             "frac": (nnz / sketch_avg_s) / red_ceiling["per_s"], "ceiling": red_ceiling}},
-            "stages_ms": {"sketch_kernel": sketch_ms / max(1, sketch_n),
-                          "contract_kernel": contract_ms / max(1, contract_n)},
-            "plain": {"ms_per_step": plain_ms, "value": world * nnz / (plain_ms / 1e3), "unit": UNIT,
-                      "speedup_countgauss_over_plain": plain_ms / ms_step},
-            "e2e": {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "call": "cg_apply_csr_host",
-                    "host_read": "auto", **e2e_modes},
-            # per step: the scatter (two kernels when deferred, three when partitioned), the
-            # contraction and its split-K sum
-            "gpu_launches": (4 if deferred else (5 if partitioned else 3)) * args.steps,
-            "clocks": clk.summary(),
-            "deterministic": {"ms_per_step": det_ms, "value": world * nnz / (det_ms / 1e3), "unit": UNIT},
+            "roofline": head["roofline"],
+            "stage_pass": head["stage_pass"],
+            "plain": head["plain"],
+            "e2e": head.get("e2e"),
+            # per step: the scatter's kernels, the contraction and its split-K sum
+            "gpu_launches": head["gpu_launches_per_step"] * args.steps,
+            "clocks": head["clocks"],
+            "deterministic": head.get("deterministic"),
             "rows": rows,
             "cpu_baseline": cpu,
         }

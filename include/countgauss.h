@@ -377,13 +377,19 @@ CG_API cg_status cg_batch_autotune(cg_batch_plan *plan, void *ws, size_t ws_byte
  * buffers by a host framework that owns every allocation, real-time loops that ban
  * cudaMalloc/cudaFree after start-up).
  *
- * Same result as cg_apply_csr (FP32 precision, atomic scatter), but every piece of
- * scratch (SX, the split-K partials, the status word) lives in one fixed device
- * array of CG_NOALLOC_SCRATCH_BYTES inside the library, which each GPU that loads the
- * library holds until the process exits.  The caller passes only inputs and Y.
- *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
- *   - The first call on a device looks up the array's device address (with that
- *     device current) and caches it; make that first call before any stream capture.
+ * Same result as cg_apply_csr (FP32 precision, atomic one-pass scatter), but every
+ * piece of scratch (SX, the split-K partials, the status word) lives in one fixed
+ * device array of CG_NOALLOC_SCRATCH_BYTES inside the library.  The caller passes only
+ * inputs and Y.
+ *   - Nothing is allocated by the call itself: no cudaMalloc, cudaFree or allocating
+ *     library call.
+ *   - The array comes into device memory with the library's module.  With lazy module
+ *     loading (the CUDA default) that happens at the first call on each device, which
+ *     also looks up the array's device address (with that device current) and caches
+ *     it per device and context; a device reset or a new context makes the next call
+ *     look it up again.  So make one call on each device at start-up, outside allocator
+ *     callbacks and before any stream capture, so that later calls only launch
+ *     kernels.  A GPU holds the array from that first call until the process exits.
  *   - Plans needing more than CG_NOALLOC_SCRATCH_BYTES of scratch (roughly
  *     B.d.4 + splits.m.d.4 + 512 bytes) are rejected with CG_ERR_WORKSPACE; other
  *     options return CG_ERR_UNSUPPORTED unless the plan is FP32 and not deterministic.
@@ -392,7 +398,8 @@ CG_API cg_status cg_batch_autotune(cg_batch_plan *plan, void *ws, size_t ws_byte
  *     streams, or two host threads) race on it and corrupt each other's results:
  *     serialise them, e.g. on one stream.
  *   - Device-side bounds reports are not surfaced here; diagnose bad inputs with
- *     cg_apply_csr and cg_plan_check. */
+ *     cg_apply_csr and cg_plan_check.  CG_OPT_TIMING records nothing for these calls
+ *     (cg_plan_timing keeps reporting the plan's other calls). */
 #define CG_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 CG_API cg_status cg_apply_csr_noalloc(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,

@@ -67,6 +67,7 @@ def _load():
                 "orc_sketch_csr": [u64, i64, i64, i64, i64, P, P, P, P],
                 "orc_sketch_dense": [u64, i64, i64, i64, i64, P, P],
                 "orc_contract": [u64, i64, i64, i64, P, P],
+                "orc_contract_range": [u64, i64, i64, i64, i64, i64, P, P],
                 "orc_apply_csr": [u64, i64, i64, i64, i64, i64, P, P, P, P, P],
                 "orc_apply_dense": [u64, i64, i64, i64, i64, i64, P, P, P],
                 "orc_plain_csr": [u64, i64, i64, i64, i64, P, P, P, i64, P, P],
@@ -187,6 +188,59 @@ def contract(seed, m, SX) -> np.ndarray:
     Y = np.zeros((m, d), np.float64)
     lib.orc_contract(seed, m, B, d, _ptr(SX), _ptr(Y))
     return Y
+
+
+def contract_range(seed, m, SX, b0, b1) -> np.ndarray:
+    """The part of G.SX that columns b0 <= b < b1 of G contribute (m x d float64)."""
+    lib = _load()
+    SX = _c(SX, np.float64)
+    B, d = SX.shape
+    Y = np.zeros((m, d), np.float64)
+    lib.orc_contract_range(seed, m, B, d, b0, b1, _ptr(SX), _ptr(Y))
+    return Y
+
+
+def _row_cuts(n, parts):
+    return [n * k // parts for k in range(parts + 1)]
+
+
+def apply_csr_parallel(seed, n, d, m, B, row_ptr, col_idx, vals, threads, row_offset=0, b_range=None):
+    """Y = G.(S.X) for CSR X with the work spread over `threads` host threads: the
+    sketch of each of `threads` row shards (global row offsets, the sharding remark of
+    Section 4) and the contraction of each of `threads` ranges of the columns of G, each
+    by the single-threaded functions above (the C calls release the interpreter lock),
+    the shards' m x d or B x d results summed in FP64.  With b_range = (b0, b1) only
+    columns b0 <= b < b1 of G are contracted (a part of the whole contraction)."""
+    from concurrent.futures import ThreadPoolExecutor
+    lib = _load()
+    rp, ci, v = _csr(row_ptr, col_idx, vals)
+    threads = max(1, int(threads))
+    cuts = _row_cuts(n, threads)
+
+    def sketch_part(k):
+        a, b = cuts[k], cuts[k + 1]
+        SXk = np.zeros((B, d), np.float64)
+        rpk = np.ascontiguousarray(rp[a:b + 1])
+        lib.orc_sketch_csr(seed, b - a, d, B, row_offset + a, _ptr(rpk), _ptr(ci), _ptr(v), _ptr(SXk))
+        return SXk
+
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(sketch_part, range(threads)))
+    SX = parts[0]
+    for P_ in parts[1:]:
+        SX += P_
+    del parts
+    b0, b1 = (0, B) if b_range is None else b_range
+    bcuts = [b0 + (b1 - b0) * k // threads for k in range(threads + 1)]
+
+    def contract_part(k):
+        Yk = np.zeros((m, d), np.float64)
+        lib.orc_contract_range(seed, m, B, d, bcuts[k], bcuts[k + 1], _ptr(SX), _ptr(Yk))
+        return Yk
+
+    with ThreadPoolExecutor(threads) as ex:
+        Ys = list(ex.map(contract_part, range(threads)))
+    return sum(Ys[1:], Ys[0])
 
 
 def apply_csr(seed, n, d, m, B, row_ptr, col_idx, vals, row_offset=0, return_sx=False):

@@ -215,21 +215,31 @@ void orc_sketch_dense(uint64_t seed, int64_t n, int64_t d, int64_t B, int64_t ro
     }
 }
 
-/* Y = G.SX with G the m x B Gaussian of tag 1 (Section 2, Theorem 1; Algorithm 1
- * step 2).  Written as the sum over b of the outer products G[:,b] SX[b,:], so that
- * each column of G is generated once.  Y is m x d row-major, overwritten. */
-void orc_contract(uint64_t seed, int64_t m, int64_t B, int64_t d, const double *SX, double *Y)
+/* The part of Y = G.SX (Section 2, Theorem 1; Algorithm 1 step 2) that columns
+ * b0 <= b < b1 of G contribute: the sum over those b of the outer products
+ * G[:,b] SX[b,:], each column of G generated once.  SX holds all B rows (B x d,
+ * row-major); Y is m x d row-major, overwritten. */
+void orc_contract_range(uint64_t seed, int64_t m, int64_t B, int64_t d, int64_t b0, int64_t b1,
+                        const double *SX, double *Y)
 {
     int64_t b, r, j;
     double *g = (double *)malloc((size_t)m * sizeof(double));
     memset(Y, 0, (size_t)(m * d) * sizeof(double));
-    for (b = 0; b < B; ++b) {
+    if (b0 < 0) b0 = 0;
+    if (b1 > B) b1 = B;
+    for (b = b0; b < b1; ++b) {
         orc_gauss_column(seed, ORC_TAG_G, m, b, g);
         for (r = 0; r < m; ++r)
             for (j = 0; j < d; ++j)
                 Y[r * d + j] += g[r] * SX[b * d + j];
     }
     free(g);
+}
+
+/* Y = G.SX with G the m x B Gaussian of tag 1: all columns b of G, in order. */
+void orc_contract(uint64_t seed, int64_t m, int64_t B, int64_t d, const double *SX, double *Y)
+{
+    orc_contract_range(seed, m, B, d, 0, B, SX, Y);
 }
 
 /* T.X = G.(S.X) for CSR X (Section 1.1; Algorithm 1 steps 1-2).  SX (B x d) is

@@ -196,6 +196,16 @@ cudaError_t launch_generate_gaussian(Key key, uint32_t tag, int64_t R, int64_t r
     return cudaGetLastError();
 }
 
+// Rows per warp chunk of the one-pass scatter: as forced, else one row per lane for small
+// inputs with under two nonzeros per row (there latency rules, and 32-row lane chunks give
+// the most CTAs: 8.8 against 9.7 us per call at 2^16 x 16 with 0.8 nonzeros per row), else
+// the kernel's own choice (staged chunks of about 96 nonzeros).
+int one_pass_rows(const cg_plan &p, int64_t nnz) {
+    if (p.scatter_rows != 0) return p.scatter_rows;
+    if (p.n > 0 && p.n <= (1 << 18) && nnz < 2 * p.n) return 1;
+    return 0;
+}
+
 }  // namespace cg
 
 using namespace cg;
@@ -376,15 +386,6 @@ cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const La
                                           timing_pair(p, CG_KERNEL_CONTRACT), st, transpose));
 }
 
-// Rows per warp chunk of the one-pass scatter: as forced, else one row per lane for small
-// inputs with under two nonzeros per row (there latency rules, and 32-row lane chunks give
-// the most CTAs: 8.8 against 9.7 us per call at 2^16 x 16 with 0.8 nonzeros per row), else
-// the kernel's own choice (staged chunks of about 96 nonzeros).
-int one_pass_rows(const cg_plan &p, int64_t nnz) {
-    if (p.scatter_rows != 0) return p.scatter_rows;
-    if (p.n > 0 && p.n <= (1 << 18) && nnz < 2 * p.n) return 1;
-    return 0;
-}
 
 // SX = S.X, or with clear = false SX += S.X (atomic and deferred scatters only).
 // host_mapped: the CSR arrays are page-locked host memory read in place (no L2 prefetch

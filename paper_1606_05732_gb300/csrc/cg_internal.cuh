@@ -134,6 +134,9 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
                                     uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, void *scratch,
                                     int *status, int ctas, int rows, const EventPair *ev, cudaStream_t stream);
 
+// Rows per warp chunk of the one-pass scatter for plan p and nnz nonzeros (cg_api.cu).
+int one_pass_rows(const cg_plan &p, int64_t nnz);
+
 // ---- deferred scatter (cg_sketch_defer.cu) -----------------------------------------
 // SX split at bucket B/2: one CSR pass reduces the lower half and writes the rest as
 // records, a second pass reduces the records (for an SX larger than the L2 holds).

@@ -13,9 +13,14 @@
 // loads the library holds these bytes until the process exits).
 //
 // Host code never dereferences `g_noalloc_scratch`: on the host the name denotes a
-// host-side shadow, not a device address, so its device address is looked up once
-// per device with cudaGetSymbolAddress (with that device current) and passed to the
-// kernels as a plain pointer.
+// host-side shadow, not a device address, so its device address is looked up with
+// cudaGetSymbolAddress (with the device current) and passed to the kernels as a plain
+// pointer.  The lookup is made once per device and context: a device reset or a new
+// context reloads the module, and the array may then sit elsewhere, so the cached address
+// is keyed by the current context's unique id (cuCtxGetId, reached through the runtime's
+// driver entry points) and looked up again when the id changes.
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "cg_internal.cuh"
@@ -29,19 +34,49 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mutex;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// The unique id of the context current on this thread (0 when there is none yet, or when
+// the driver does not offer the calls).
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up on the first call
+// in each context (the lookup loads this file's module if it is not loaded yet).
 cudaError_t scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (g_scratch_ptr[dev] == nullptr) {
+    const unsigned long long ctx = current_context_id();
+    if (g_scratch_ptr[dev] == nullptr || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = current_context_id();  // the lookup made the context current if none was
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -80,7 +115,8 @@ extern "C" cg_status cg_apply_csr_noalloc(cg_plan *p, const int32_t *row_ptr, co
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return CG_ERR_CUDA;
     if (launch_sketch_csr_atomic(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B),
                                  static_cast<int>(nnz), make_key(p->seed), p->row_offset, SX, status,
-                                 static_cast<int>(p->sketch_ctas), p->scatter_passes, p->scatter_rows, nullptr, st) != cudaSuccess)
+                                 static_cast<int>(p->sketch_ctas), p->scatter_passes, one_pass_rows(*p, nnz), nullptr,
+                                 st) != cudaSuccess)
         return CG_ERR_CUDA;
     if (launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), nsplit, partials, Y, nullptr, st) !=
         cudaSuccess)

@@ -120,22 +120,29 @@ __global__ void __launch_bounds__(kThreads) zero_fill_kernel(float *__restrict__
 // integer order is its numeric order) combined with atomicMax.  The values up to the
 // first 16-byte boundary and past the last one are read one by one, the rest as float4
 // with four loads in flight per thread.
-__device__ __forceinline__ float finite_abs_max(float mx, float v) {
-    const float a = fabsf(v);
-    return a <= 3.0e38f ? fmaxf(mx, a) : mx;  // finite values only
+__device__ __forceinline__ bool is_finite_bits(float v) { return (__float_as_uint(v) & 0x7F800000u) != 0x7F800000u; }
+
+// max of mx and |v| over finite v; a non-finite v sets `special` instead.
+__device__ __forceinline__ float finite_abs_max(float mx, float v, bool &special) {
+    if (!is_finite_bits(v)) {
+        special = true;
+        return mx;
+    }
+    return fmaxf(mx, fabsf(v));
 }
 
 __global__ void __launch_bounds__(kThreads)
 absmax_kernel(const float *__restrict__ x, int64_t count, int *__restrict__ maxbits) {
     float mx = 0.0f;
+    bool sp = false;  // a NaN or an infinity seen
     const int64_t tid = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x;
     const int64_t nthreads = static_cast<int64_t>(gridDim.x) * kThreads;
     const int64_t lead = static_cast<int64_t>(((16 - (reinterpret_cast<uintptr_t>(x) & 15)) & 15) / 4);
     const int64_t head = lead < count ? lead : count;
     const int64_t quads = (count - head) / 4;
     const int64_t tail0 = head + 4 * quads;
-    if (tid < head) mx = finite_abs_max(mx, __ldg(x + tid));
-    if (tail0 + tid < count) mx = finite_abs_max(mx, __ldg(x + tail0 + tid));
+    if (tid < head) mx = finite_abs_max(mx, __ldg(x + tid), sp);
+    if (tail0 + tid < count) mx = finite_abs_max(mx, __ldg(x + tail0 + tid), sp);
     const float4 *q = reinterpret_cast<const float4 *>(x + head);
     int64_t i = tid;
     for (; i + 3 * nthreads < quads; i += 4 * nthreads) {
@@ -144,15 +151,48 @@ absmax_kernel(const float *__restrict__ x, int64_t count, int *__restrict__ maxb
         for (int u = 0; u < 4; ++u) v[u] = __ldg(q + i + u * nthreads);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            mx = finite_abs_max(finite_abs_max(finite_abs_max(finite_abs_max(mx, v[u].x), v[u].y), v[u].z), v[u].w);
+            mx = finite_abs_max(finite_abs_max(finite_abs_max(finite_abs_max(mx, v[u].x, sp), v[u].y, sp), v[u].z, sp),
+                                v[u].w, sp);
     }
     for (; i < quads; i += nthreads) {
         const float4 v = __ldg(q + i);
-        mx = finite_abs_max(finite_abs_max(finite_abs_max(finite_abs_max(mx, v.x), v.y), v.z), v.w);
+        mx = finite_abs_max(finite_abs_max(finite_abs_max(finite_abs_max(mx, v.x, sp), v.y, sp), v.z, sp), v.w, sp);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0f) atomicMax(maxbits, __float_as_int(mx));
+    if (__any_sync(0xffffffffu, sp) && (threadIdx.x & 31) == 0) atomicOr(maxbits + 1, 1);
+}
+
+// The rule for NaN and infinite values, as IEEE addition applies it in the fp32 scatters:
+// the fixed-point sums take finite values only (to_fixed maps the others to 0), so when
+// the max-|x| pass saw any (maxbits[1] != 0) this pass adds every non-finite entry to its
+// cell of the rounded SX.  Whatever the order, a cell that receives a NaN, or both +Inf
+// and -Inf, becomes NaN, and one that receives infinities of one sign becomes that
+// infinity, so the result stays run-to-run reproducible.  Each such entry finds its row by
+// binary search over row_ptr; column indices out of range are skipped (the scatter
+// reported them).
+__global__ void __launch_bounds__(kThreads)
+add_nonfinite_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
+                     int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, const int *__restrict__ maxbits,
+                     float *__restrict__ SX) {
+    if (maxbits[1] == 0) return;
+    for (int k = blockIdx.x * kThreads + threadIdx.x; k < nnz; k += gridDim.x * kThreads) {
+        const float v = __ldg(vals + k);
+        if (is_finite_bits(v)) continue;
+        const int j = __ldg(col_idx + k);
+        if (static_cast<unsigned>(j) >= static_cast<unsigned>(d)) continue;
+        int lo = 0, hi = n - 1;  // the last row i < n with row_ptr[i] <= k
+        while (lo < hi) {
+            const int mid = lo + (hi - lo + 1) / 2;
+            if (__ldg(row_ptr + mid) <= k) lo = mid; else hi = mid - 1;
+        }
+        if (!(__ldg(row_ptr + lo) <= k && k < __ldg(row_ptr + lo + 1))) continue;  // malformed offsets
+        uint32_t h;
+        float sg;
+        hash_sign(key, static_cast<uint64_t>(row_offset + lo), B, h, sg);
+        atomicAdd(SX + static_cast<size_t>(h) * d + j, sg * v);
+    }
 }
 
 // SX = (float)(acc 2^-F): one rounding of the exact fixed-point sums.
@@ -346,6 +386,9 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
     const int64_t blocks = (cells + kThreads - 1) / kThreads;
     fixed_to_float_kernel<<<static_cast<unsigned>(blocks < sms * 8 ? (blocks > 0 ? blocks : 1) : sms * 8), kThreads, 0,
                             stream>>>(acc, cells, maxbits, nnz, SX);
+    if (nnz > 0 && n > 0)
+        add_nonfinite_kernel<<<sms * 2, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                               maxbits, SX);
     record(ev, false, stream);
     return cudaGetLastError();
 }

@@ -28,9 +28,27 @@ def test_reference_arm_prints_one_contract_line():
     assert j["steps"] == 2 and j["warmup"] == 1 and j["n_gpus"] == 1
     assert j["value"] > 0 and j["ms_per_step"] > 0 and j["dtype"] == "f64"
     assert j["config"]["workload"] == "small_n65536_d16" and j["config"]["d"] == 16
-    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] == 1
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] == bench_cores()
     assert j["cpu_baseline"]["value"] == j["value"]
+    assert 0 < j["config"]["fraction_per_step"] <= 1 / 16
     assert j["e2e"] == {"value": j["value"], "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def bench_cores():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.host_cores()
+
+
+def test_oracle_fraction_step_does_that_fraction_of_the_work():
+    """A reference step on fraction f runs the sketch of the first f n rows and the
+    contraction over the first f B columns of G: its nonzero count is that of those rows."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1606_05732_gb300 import synth
+    X, w = synth.workload_csr("small_n65536_d16")
+    dt, k1 = bench.oracle_fraction_step(X, w, 0.25, 2)
+    assert dt > 0 and k1 == int(X.row_ptr[X.n // 4])
 
 
 def test_reference_arm_other_ranks_print_nothing():

@@ -121,3 +121,33 @@ def test_fullsize_grad_dense_forward_and_adjoints():
     err_s = rel(dXs, oracle.adjoint_csr(seed, n, m, B, Xs.row_ptr, Xs.col_idx, dY64))
     print(f"grad_n1M_d64: forward {err_f:.3e}, dense adjoint {err_d:.3e}, CSR adjoint {err_s:.3e}")
     assert err_f < FP32_TOL and err_d < FP32_TOL and err_s < FP32_TOL
+
+
+def test_fullsize_deterministic_mode_nmf():
+    """Deterministic mode at the NMF-like workload's full size (53.7 M nonzeros, the
+    largest nnz of its tests, so the coarsest fixed-point resolution): two runs are
+    bit-identical and every SX entry is within one fp32 ulp plus the fixed-point
+    resolution per term (2^(L+e-62), 2^e > max|x|, 2^L > nnz) of the oracle's FP64 sum."""
+    from paper_1606_05732_gb300 import countgauss
+    X, w = synth.workload_csr("nmf_n16M_d64")
+    dev = torch.device("cuda", 0)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).to(dev)
+    ci = torch.from_numpy(X.col_idx).to(dev)
+    v = torch.from_numpy(X.vals).to(dev)
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"], deterministic=True)
+    SX1 = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    SX2 = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    del rp, ci, v
+    np.testing.assert_array_equal(SX1, SX2)
+    Yo, SXo = oracle.apply_csr(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    want = SXo.astype(np.float32)
+    L = max(1, int(X.nnz).bit_length())
+    e = int(np.frexp(np.abs(X.vals).max())[1])
+    per_term = 2.0 ** (L + e - 62)
+    rows_per_bucket = np.bincount(oracle.hash_sign(w["seed"], w["B"], 0, X.n)[0], minlength=w["B"])
+    bound = np.spacing(np.abs(want)).astype(np.float64) + (rows_per_bucket[:, None] + 1) * per_term
+    assert (np.abs(SX1.astype(np.float64) - SXo) <= bound).all()
+    assert (SX1 == want).mean() > 0.99
+    assert rel(Y, Yo) < FP32_TOL

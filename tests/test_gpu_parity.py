@@ -150,6 +150,55 @@ def test_deterministic_mode_is_bit_reproducible_and_exact(n, d, m, B, seed, kind
     assert rel(Y1, Yo) < FP32_TOL
 
 
+def _nan_inf_equal(got, want):
+    """Same NaN positions, same infinities (with sign), finite entries within 1e-6."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(want))
+    np.testing.assert_array_equal(np.isposinf(got), np.isposinf(want))
+    np.testing.assert_array_equal(np.isneginf(got), np.isneginf(want))
+    fin = np.isfinite(want)
+    assert rel(got[fin], want[fin]) < 1e-6
+
+
+@pytest.mark.parametrize("mode", ["atomic", "deferred", "binned", "partition", "deterministic"])
+def test_nonfinite_values_propagate_as_ieee_addition(mode):
+    """The rule for NaN and infinite entries of X, the same in every scatter: the SX cell
+    they land in is NaN if it receives a NaN or both +Inf and -Inf, else the infinity it
+    receives (IEEE addition, as the FP64 oracle computes it); every other cell is unchanged.
+    The deterministic mode keeps its bit-reproducible result."""
+    n, d, m, B, seed = 20000, 16, 8, 512, 5
+    Xd = synth.csr_bernoulli(n, d, 0.05, seed=6).to_dense()
+    h, sg = oracle.hash_sign(seed, B, 0, n)
+    # two rows sharing a bucket: +Inf from one and -Inf from the other into one cell
+    first = {}
+    pair = None
+    for i in range(n):
+        if h[i] in first:
+            pair = (first[h[i]], i)
+            break
+        first[h[i]] = i
+    i1, i2 = pair
+    Xd[i1, 3] = np.inf * sg[i1]
+    Xd[i2, 3] = -np.inf * sg[i2]
+    Xd[777, 5] = np.nan
+    Xd[1234, 0] = np.inf
+    Xd[1234, 1] = -np.inf
+    X = synth.csr_from_dense(Xd)
+    rp, ci, v = dev_csr(X)
+    kw = {"deterministic": True} if mode == "deterministic" else {"scatter": mode}
+    plan = cg().CountGauss(n, d, m, B, seed, **kw)
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    assert np.isnan(SXo[h[i1], 3]) and np.isnan(SXo).sum() == 2 and np.isinf(SXo).sum() == 2
+    _nan_inf_equal(SX, SXo)
+    _nan_inf_equal(Y, Yo)
+    if mode == "deterministic":
+        np.testing.assert_array_equal(plan.sketch_csr(rp, ci, v).cpu().numpy(), SX)
+
+
 def test_deterministic_scale_sees_every_value_at_any_alignment():
     """The fixed-point scale comes from max |x| over all stored values; the largest value
     placed first, second, third, second-last or last, with the values starting at each

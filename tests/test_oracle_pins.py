@@ -222,6 +222,29 @@ def test_brute_force_dense_T(n, d, m, B, seed):
     assert rel(Yd, T @ Xd) < 1e-13
 
 
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_contract_range_and_parallel_apply_against_materialised_T(threads):
+    """The contraction restricted to columns [b0, b1) of G is G[:, b0:b1] SX[b0:b1] with G
+    materialised; the host-parallel apply (row shards with global offsets, column ranges
+    of G, shards summed) equals T.X with S and G materialised, with and without a row
+    offset, and a range of G's columns gives that part of G.SX."""
+    n, d, m, B, seed = 203, 6, 9, 37, 7
+    X = synth.csr_ragged(n, d, seed=11)
+    Xd = X.to_dense()
+    G = oracle.gaussian_G(seed, m, B)
+    SX = oracle.sketch_csr(seed, n, d, B, X.row_ptr, X.col_idx, X.vals)
+    for b0, b1 in [(0, B), (0, 1), (5, 20), (36, 37), (10, 10)]:
+        want = G[:, b0:b1] @ SX[b0:b1]
+        got = oracle.contract_range(seed, m, SX, b0, b1)
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
+    for off in (0, 1000):
+        T = G @ dense_S(seed, n + off, B)[:, off:]
+        got = oracle.apply_csr_parallel(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, threads, row_offset=off)
+        assert rel(got, T @ Xd) < 1e-13
+    part = oracle.apply_csr_parallel(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, threads, b_range=(4, 30))
+    assert rel(part, G[:, 4:30] @ SX[4:30]) < 1e-13
+
+
 def test_brute_force_plain():
     n, d, m, seed = 70, 6, 9, 5
     X = synth.csr_ragged(n, d, seed=4)
