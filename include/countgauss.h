@@ -293,10 +293,21 @@ CG_API cg_status cg_row_argmax_argmin(const float *Z, int32_t m, int32_t d, int3
                                       void *stream);
 
 /* Algorithm 1 steps 1-3 for CSR X: Z = T.X as cg_apply_csr (Z device m x d, workspace
- * of CG_OP_APPLY_CSR), then the row argmax / argmin of Z. */
+ * of CG_OP_APPLY_CSR), and the row argmax / argmin of Z (imax, imin: device int32[m],
+ * lowest column on ties) taken by the split-K sum itself, which gives each row of Z to
+ * one thread block: no separate pass over Z.  The sums run in a fixed order per row, so
+ * Z is reproducible; it may differ from cg_apply_csr's Z in the last bits (another fixed
+ * order).  Errors as cg_apply_csr, and CG_ERR_INVALID_ARG for null or misaligned imax /
+ * imin. */
 CG_API cg_status cg_nmf_anchors_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                                     int64_t nnz, float *Z, int32_t *imax, int32_t *imin, void *ws, size_t ws_bytes,
                                     void *stream);
+
+/* The same with int64 row offsets (as cg_apply_csr_i64; workspace of
+ * CG_OP_APPLY_CSR_I64). */
+CG_API cg_status cg_nmf_anchors_csr_i64(cg_plan *plan, const int64_t *row_ptr, const int32_t *col_idx,
+                                        const float *vals, int64_t nnz, float *Z, int32_t *imax, int32_t *imin,
+                                        void *ws, size_t ws_bytes, void *stream);
 
 /* ---- distribution checker ----------------------------------------------------------- */
 

@@ -62,6 +62,7 @@ SIGNATURES = {
     "cg_contract": [P, P, P, P, SZ, P],
     "cg_row_argmax_argmin": [P, I32, I32, P, P, P],
     "cg_nmf_anchors_csr": [P, P, P, P, I64, P, P, P, P, SZ, P],
+    "cg_nmf_anchors_csr_i64": [P, P, P, P, I64, P, P, P, P, SZ, P],
     "cg_moments_f64": [P, I64, I32, P, P, P],
     "cg_batch_plan_create": [P, I32, ctypes.POINTER(P)],
     "cg_batch_plan_destroy": [P],

@@ -237,12 +237,11 @@ class CountGauss:
 
     def nmf_anchors(self, row_ptr, col_idx, vals):
         """Algorithm 1 steps 1-3: Z = T.X and, per row of Z, the column of its max and
-        of its min (lowest index on ties).  Returns (Z, imax, imin).  With int64 row_ptr
-        (2^31 nonzeros or more): cg_apply_csr_i64, then cg_row_argmax_argmin."""
-        if torch.is_tensor(row_ptr) and row_ptr.dtype == torch.int64:
-            Z = self.apply_csr(row_ptr, col_idx, vals)
-            return (Z, *row_argmax_argmin(Z))
-        row_ptr = _need(row_ptr, torch.int32, "row_ptr")
+        of its min (lowest index on ties), taken inside the split-K sum.  Returns
+        (Z, imax, imin).  int64 row_ptr (2^31 nonzeros or more) runs
+        cg_nmf_anchors_csr_i64."""
+        wide = torch.is_tensor(row_ptr) and row_ptr.dtype == torch.int64
+        row_ptr = _need(row_ptr, torch.int64 if wide else torch.int32, "row_ptr")
         col_idx = _need(col_idx, torch.int32, "col_idx")
         vals = _need(vals, torch.float32, "vals")
         dev = row_ptr.device
@@ -250,8 +249,9 @@ class CountGauss:
         Z = torch.empty(self.m, self.d, dtype=torch.float32, device=dev)
         imax = torch.empty(self.m, dtype=torch.int32, device=dev)
         imin = torch.empty(self.m, dtype=torch.int32, device=dev)
-        ws = self.workspace(_lib.OP_APPLY_CSR, nnz, dev)
-        _lib.check("cg_nmf_anchors_csr", self._lib.cg_nmf_anchors_csr(
+        ws = self.workspace(_lib.OP_APPLY_CSR_I64 if wide else _lib.OP_APPLY_CSR, nnz, dev)
+        name = "cg_nmf_anchors_csr_i64" if wide else "cg_nmf_anchors_csr"
+        _lib.check(name, getattr(self._lib, name)(
             self._h, _ptr(row_ptr), _ptr(col_idx), _ptr(vals), nnz, _ptr(Z), _ptr(imax), _ptr(imin), _ptr(ws),
             ws.numel(), _stream(dev)))
         return Z, imax, imin

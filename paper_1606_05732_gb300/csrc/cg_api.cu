@@ -374,16 +374,18 @@ cg_status check_csr(const cg_plan *p, const int32_t *row_ptr, const int32_t *col
 int *status_word(void *ws) { return reinterpret_cast<int *>(ws); }
 char *region(void *ws, size_t off) { return reinterpret_cast<char *>(ws) + off; }
 
-// Y = G.SX (m x d), or with `transpose` its transpose (d x m).
+// Y = G.SX (m x d), or with `transpose` its transpose (d x m); with imax / imin also the
+// row argmax / argmin of Y, from the split-K sum itself (Algorithm 1 step 3).
 cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const Layout &L, cudaStream_t st,
-                       bool transpose = false) {
+                       bool transpose = false, int32_t *imax = nullptr, int32_t *imin = nullptr) {
     if (p->precision != CG_PREC_FP32)
         return from_cuda(launch_contract_tc(SX, p->m, p->d, p->B, make_key(p->seed), p->precision,
                                             contract_tc_splits(*p), reinterpret_cast<float *>(region(ws, L.b_off)),
-                                            Y, status_word(ws), timing_pair(p, CG_KERNEL_CONTRACT), st, transpose));
+                                            Y, status_word(ws), timing_pair(p, CG_KERNEL_CONTRACT), st, transpose,
+                                            imax, imin));
     return from_cuda(launch_contract_ffma(SX, p->m, p->d, p->B, make_key(p->seed), contract_splits(*p),
                                           reinterpret_cast<float *>(region(ws, L.b_off)), Y,
-                                          timing_pair(p, CG_KERNEL_CONTRACT), st, transpose));
+                                          timing_pair(p, CG_KERNEL_CONTRACT), st, transpose, imax, imin));
 }
 
 
@@ -768,6 +770,38 @@ cg_status cg_apply_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *co
     cudaStream_t st = as_stream(stream);
     if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, st, true)) != CG_OK) return s;
     return run_contract(p, SX, Y, ws, L, st);
+}
+
+cg_status cg_nmf_anchors_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
+                             int64_t nnz, float *Z, int32_t *imax, int32_t *imin, void *ws, size_t ws_bytes,
+                             void *stream) {
+    cg::NvtxRange nvtx_range("cg_nmf_anchors_csr");
+    if (p == nullptr || Z == nullptr || imax == nullptr || imin == nullptr || misaligned(Z, 4)) return CG_ERR_INVALID_ARG;
+    if (misaligned(imax, 4) || misaligned(imin, 4)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr(p, row_ptr, col_idx, vals, nnz, true);
+    if (s != CG_OK) return s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_APPLY_CSR, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    if ((s = run_sketch_csr(p, row_ptr, col_idx, vals, nnz, SX, ws, L, st)) != CG_OK) return s;
+    return run_contract(p, SX, Z, ws, L, st, false, imax, imin);
+}
+
+cg_status cg_nmf_anchors_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
+                                 int64_t nnz, float *Z, int32_t *imax, int32_t *imin, void *ws, size_t ws_bytes,
+                                 void *stream) {
+    cg::NvtxRange nvtx_range("cg_nmf_anchors_csr_i64");
+    if (p == nullptr || Z == nullptr || imax == nullptr || imin == nullptr || misaligned(Z, 4)) return CG_ERR_INVALID_ARG;
+    if (misaligned(imax, 4) || misaligned(imin, 4)) return CG_ERR_INVALID_ARG;
+    cg_status s = check_csr_i64(p, row_ptr, col_idx, vals, nnz);
+    if (s != CG_OK) return s;
+    Layout L;
+    if ((s = check_ws(p, CG_OP_APPLY_CSR_I64, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
+    float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
+    cudaStream_t st = as_stream(stream);
+    if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, st, true)) != CG_OK) return s;
+    return run_contract(p, SX, Z, ws, L, st, false, imax, imin);
 }
 
 cg_status cg_sketch_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,

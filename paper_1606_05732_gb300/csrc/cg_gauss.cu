@@ -91,6 +91,108 @@ reduce_splits_kernel(const float *__restrict__ part, int nsplit, int64_t total, 
     }
 }
 
+// The split-K sum fused with Algorithm 1 step 3: CTA r owns row r of Y (m x d) and sums
+// its splits in a fixed order -- the row's columns in chunks of 32 (one lane each), W
+// warps per chunk with warp w taking partials s = w, w + W, ... in increasing s, the W
+// sums then added in increasing w -- writes the row, and takes its argmax and argmin in
+// the same pass, ties to the lowest column (strict comparisons in increasing column
+// order, lowest index between equal values in the reductions).  A NaN is never chosen;
+// a row with no ordered value reports column 0.
+constexpr int kRowThreads = 1024;
+
+__global__ void __launch_bounds__(kRowThreads)
+reduce_rows_anchors_kernel(const float *__restrict__ part, int nsplit, int m, int d, float *__restrict__ Y,
+                           int32_t *__restrict__ imax, int32_t *__restrict__ imin) {
+    pdl_wait();  // the partials come from the kernel launched before
+    constexpr int kWarps = kRowThreads / 32;
+    __shared__ float red[kWarps][33];
+    __shared__ float s_v[2][kWarps];
+    __shared__ int s_j[2][kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x;
+    const int64_t total = static_cast<int64_t>(m) * d;
+    const int chunks = (d + 31) / 32;
+    const int per_round = chunks < kWarps ? chunks : kWarps;  // chunks summed at once
+    const int W = kWarps / per_round;                         // warps per chunk
+    const int ci = warp / W, slot = warp % W;
+    float vmax = -INFINITY, vmin = INFINITY;
+    int jmax = d, jmin = d;
+    for (int c0 = 0; c0 < chunks; c0 += per_round) {
+        const int c = c0 + ci;
+        const int j = c * 32 + lane;
+        const bool live = ci < per_round && c < chunks && j < d;
+        float acc = 0.0f;
+        if (live) {
+            const float *p = part + static_cast<int64_t>(r) * d + j;
+            int s = slot;
+            for (; s + 3 * W < nsplit; s += 4 * W) {
+                const float a0 = __ldg(p + static_cast<int64_t>(s) * total);
+                const float a1 = __ldg(p + static_cast<int64_t>(s + W) * total);
+                const float a2 = __ldg(p + static_cast<int64_t>(s + 2 * W) * total);
+                const float a3 = __ldg(p + static_cast<int64_t>(s + 3 * W) * total);
+                acc += a0;
+                acc += a1;
+                acc += a2;
+                acc += a3;
+            }
+            for (; s < nsplit; s += W) acc += __ldg(p + static_cast<int64_t>(s) * total);
+        }
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (slot == 0 && live) {
+            float y = red[warp][lane];
+            for (int q = 1; q < W; ++q) y += red[warp + q][lane];
+            Y[static_cast<int64_t>(r) * d + j] = y;
+            if (y > vmax) {  // columns reach a lane in increasing order: the first wins ties
+                vmax = y;
+                jmax = j;
+            }
+            if (y < vmin) {
+                vmin = y;
+                jmin = j;
+            }
+        }
+        __syncthreads();
+    }
+    // lanes, then warps: the larger (smaller) value, the lower column between equal ones
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float omax = __shfl_xor_sync(0xffffffffu, vmax, o);
+        const int ojmax = __shfl_xor_sync(0xffffffffu, jmax, o);
+        const float omin = __shfl_xor_sync(0xffffffffu, vmin, o);
+        const int ojmin = __shfl_xor_sync(0xffffffffu, jmin, o);
+        if (omax > vmax || (omax == vmax && ojmax < jmax)) {
+            vmax = omax;
+            jmax = ojmax;
+        }
+        if (omin < vmin || (omin == vmin && ojmin < jmin)) {
+            vmin = omin;
+            jmin = ojmin;
+        }
+    }
+    if (lane == 0) {
+        s_v[0][warp] = vmax;
+        s_j[0][warp] = jmax;
+        s_v[1][warp] = vmin;
+        s_j[1][warp] = jmin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarps; ++w) {
+            if (s_v[0][w] > vmax || (s_v[0][w] == vmax && s_j[0][w] < jmax)) {
+                vmax = s_v[0][w];
+                jmax = s_j[0][w];
+            }
+            if (s_v[1][w] < vmin || (s_v[1][w] == vmin && s_j[1][w] < jmin)) {
+                vmin = s_v[1][w];
+                jmin = s_j[1][w];
+            }
+        }
+        imax[r] = jmax < d ? jmax : 0;
+        imin[r] = jmin < d ? jmin : 0;
+    }
+}
+
 template <int W>
 cudaError_t launch_reduce_w(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream,
                             int tr_cols) {
@@ -131,6 +233,14 @@ size_t contract_partials_bytes(const cg_plan &p) {
     return static_cast<size_t>(splits) * p.m * p.d * sizeof(float);
 }
 
+cudaError_t launch_reduce_rows_anchors(const float *partials, int nsplit, int m, int d, float *Y, int32_t *imax,
+                                      int32_t *imin, cudaStream_t stream) {
+    if (m == 0) return cudaSuccess;
+    const cudaError_t e = launch_after_previous(reduce_rows_anchors_kernel, dim3(static_cast<unsigned>(m)),
+                                                dim3(kRowThreads), 0, stream, partials, nsplit, m, d, Y, imax, imin);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream,
                                  int tr_cols) {
     if (total == 0) return cudaSuccess;
@@ -144,7 +254,8 @@ cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t tota
 }
 
 cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials,
-                                 float *Y, const EventPair *ev, cudaStream_t stream, bool transpose) {
+                                 float *Y, const EventPair *ev, cudaStream_t stream, bool transpose, int32_t *imax,
+                                 int32_t *imin) {
     const int64_t nslabs = (B + kKT - 1) / kKT;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
@@ -164,6 +275,7 @@ cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key k
     record(ev, false, stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (imax != nullptr) return launch_reduce_rows_anchors(partials, used, m, d, Y, imax, imin, stream);
     return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream, transpose ? d : 0);
 }
 

@@ -81,8 +81,13 @@ struct Cfg {
 template <int NT, bool SPLIT3>
 constexpr int bf16_threads() { return SPLIT3 && NT >= 128 ? 512 : 256; }
 
+// Resident CTAs per SM the register budget is sized for: three for the single-bf16 form
+// with N tiles of at most 128 (its stages fit three times in shared memory), else one.
 template <int NT, bool SPLIT3>
-__global__ void __launch_bounds__(bf16_threads<NT, SPLIT3>(), 1)
+constexpr int bf16_min_ctas() { return !SPLIT3 && NT <= 128 ? 3 : 1; }
+
+template <int NT, bool SPLIT3>
+__global__ void __launch_bounds__(bf16_threads<NT, SPLIT3>(), bf16_min_ctas<NT, SPLIT3>())
 contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Key key, int64_t slabs_per_cta,
                         float *__restrict__ part, int *__restrict__ status) {
     pdl_wait();  // SX comes from the scatter launched before
@@ -140,6 +145,22 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
         uint8_t *a_lo = stage + C::kA + C::kB;
         uint8_t *b_lo = a_lo + C::kA;
 
+        // B^T = SX[k0 .. k0+64, n0 .. n0+NT) stored [n][k]: its loads are issued first, so
+        // that they are in flight while the G tile is drawn, and stored after it.
+        constexpr int kThr = bf16_threads<NT, SPLIT3>();
+        constexpr int kBq = (NT * (kBK / 4) + kThr - 1) / kThr;  // quads of SX per thread
+        float xs[kBq][4];
+#pragma unroll
+        for (int j = 0; j < kBq; ++j) {
+            const int q = t + j * kThr;
+            const int nl = q % NT;
+            const int kq = q / NT;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t krow = k0 + 4 * kq + c;
+                xs[j][c] = (q < NT * (kBK / 4) && krow < B && nl < bn) ? __ldg(SX + krow * d + n0 + nl) : 0.0f;
+            }
+        }
         // A = G[m0 .. m0+128, k0 .. k0+64): blocks of 4 rows (one Philox call) x 4 columns.
         for (int q = t; q < (kM / 4) * (kBK / 4); q += bf16_threads<NT, SPLIT3>()) {
             const int gl = q >> 4;
@@ -150,7 +171,9 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
             for (int c = 0; c < 4; ++c) {
                 const int64_t col = k0 + 4 * kq + c;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g < groups && col < B) v = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(col), g);
+                // one bf16 per entry: G drawn with the fast intrinsics; the split form keeps the
+                // fp32-accurate G its two bf16 terms resolve
+                if (g < groups && col < B) v = gauss_quad<!SPLIT3>(key, kTagG, groups, static_cast<uint64_t>(col), g);
                 z[c][0] = v.x;
                 z[c][1] = v.y;
                 z[c][2] = v.z;
@@ -170,17 +193,15 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
                         make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
             }
         }
-        // B^T = SX[k0 .. k0+64, n0 .. n0+NT) stored [n][k].
-        for (int q = t; q < NT * (kBK / 4); q += bf16_threads<NT, SPLIT3>()) {
+#pragma unroll
+        for (int j = 0; j < kBq; ++j) {
+            const int q = t + j * kThr;
+            if (q >= NT * (kBK / 4)) break;
             const int nl = q % NT;
             const int kq = q / NT;
             float h[4], l[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int64_t krow = k0 + 4 * kq + c;
-                const float x = (krow < B && nl < bn) ? __ldg(SX + krow * d + n0 + nl) : 0.0f;
-                split_bf16(x, h[c], l[c]);
-            }
+            for (int c = 0; c < 4; ++c) split_bf16(xs[j][c], h[c], l[c]);
             const uint32_t off = tc::sw128_bf16(nl, 4 * kq);
             *reinterpret_cast<uint2 *>(b_hi + off) = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
             if (SPLIT3)
@@ -425,7 +446,8 @@ contract_tc_fp8_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Ke
             for (int c = 0; c < 4; ++c) {
                 const int64_t col = k0 + 4 * kq + c;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g < groups && col < B) v = gauss_quad(key, kTagG, groups, static_cast<uint64_t>(col), g);
+                // e4m3 keeps 3 mantissa bits (x3: about 7): G drawn with the fast intrinsics
+                if (g < groups && col < B) v = gauss_quad<true>(key, kTagG, groups, static_cast<uint64_t>(col), g);
                 z[c][0] = v.x;
                 z[c][1] = v.y;
                 z[c][2] = v.z;
@@ -588,7 +610,7 @@ int contract_tc_splits(const cg_plan &p) {
 
 cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
                                float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream,
-                               bool transpose) {
+                               bool transpose, int32_t *imax, int32_t *imin) {
     cudaError_t e;
     const bool fp8 = precision == CG_PREC_FP8_E4M3 || precision == CG_PREC_FP8X3;
     const int nt = fp8 ? tc8_nt(d) : tc_nt(d);
@@ -614,6 +636,7 @@ cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key
     const int64_t nslabs = (B + bk - 1) / bk;
     const int64_t per = (nslabs + nsplit - 1) / nsplit;
     const int used = static_cast<int>((nslabs + per - 1) / per);
+    if (imax != nullptr) return launch_reduce_rows_anchors(partials, used, m, d, Y, imax, imin, stream);
     return launch_reduce_splits(partials, used, static_cast<int64_t>(m) * d, Y, stream, transpose ? d : 0);
 }
 

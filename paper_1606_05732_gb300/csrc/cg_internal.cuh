@@ -181,18 +181,25 @@ cudaError_t launch_sketch_csr_partitioned(const int *row_ptr, const int *col_idx
 // Y = G.SX (m x d row-major), or with `transpose` its transpose (d x m row-major).
 int contract_splits(const cg_plan &p);
 size_t contract_partials_bytes(const cg_plan &p);
+// With imax / imin the split-K sum is the row-owned one that also writes, per row of Y,
+// the column of its maximum and of its minimum (Algorithm 1 step 3).
 cudaError_t launch_contract_ffma(const float *SX, int m, int d, int64_t B, Key key, int nsplit, float *partials,
-                                 float *Y, const EventPair *ev, cudaStream_t stream, bool transpose = false);
+                                 float *Y, const EventPair *ev, cudaStream_t stream, bool transpose = false,
+                                 int32_t *imax = nullptr, int32_t *imin = nullptr);
 // Y = fixed-order sum of nsplit partials of `total` floats; with tr_cols > 0 the
 // (total / tr_cols) x tr_cols result is stored transposed.
 cudaError_t launch_reduce_splits(const float *partials, int nsplit, int64_t total, float *Y, cudaStream_t stream,
                                  int tr_cols = 0);
+// Y (m x d) = fixed-order sum of nsplit partials, one CTA per row, with each row's argmax
+// and argmin columns (lowest index on ties) into imax[m], imin[m].
+cudaError_t launch_reduce_rows_anchors(const float *partials, int nsplit, int m, int d, float *Y, int32_t *imax,
+                                      int32_t *imin, cudaStream_t stream);
 
 // ---- tensor-core contraction (cg_gauss_tc.cu) -----------------------------------
 int contract_tc_splits(const cg_plan &p);
 cudaError_t launch_contract_tc(const float *SX, int m, int d, int64_t B, Key key, int precision, int nsplit,
                                float *partials, float *Y, int *status, const EventPair *ev, cudaStream_t stream,
-                               bool transpose = false);
+                               bool transpose = false, int32_t *imax = nullptr, int32_t *imin = nullptr);
 
 // ---- right projection Z = A.T^T (cg_right.cu) -------------------------------------
 // Scratch bytes of the scatter of a rows x n CSR matrix with nnz nonzeros (the table of

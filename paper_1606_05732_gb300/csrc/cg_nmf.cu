@@ -1,6 +1,7 @@
-// cg_nmf.cu -- Algorithm 1 ("CountGauss NMF") step 3: for every row r of Z = T.X,
-// the column index of its maximum and of its minimum (the anchor candidates I_max,
-// I_min).  Ties go to the lowest column index.  Z comes from steps 1-2 (cg_apply_csr).
+// cg_nmf.cu -- Algorithm 1 ("CountGauss NMF") step 3 on a given Z: for every row r, the
+// column index of its maximum and of its minimum (the anchor candidates I_max, I_min),
+// ties to the lowest column index.  Steps 1-3 in one go (cg_nmf_anchors_csr, in
+// cg_api.cu) take the argmax / argmin inside the split-K sum instead.
 #include "cg_internal.cuh"
 
 namespace cg {
@@ -65,14 +66,4 @@ extern "C" cg_status cg_row_argmax_argmin(const float *Z, int32_t m, int32_t d, 
                                                 reinterpret_cast<cudaStream_t>(stream), Z, m, d, imax, imin);
     if (e != cudaSuccess) return CG_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ERR_CUDA;
-}
-
-extern "C" cg_status cg_nmf_anchors_csr(cg_plan *plan, const int32_t *row_ptr, const int32_t *col_idx,
-                                        const float *vals, int64_t nnz, float *Z, int32_t *imax, int32_t *imin,
-                                        void *ws, size_t ws_bytes, void *stream) {
-    cg::NvtxRange nvtx_range("cg_nmf_anchors_csr");
-    if (plan == nullptr) return CG_ERR_INVALID_ARG;
-    const cg_status s = cg_apply_csr(plan, row_ptr, col_idx, vals, nnz, Z, ws, ws_bytes, stream);
-    if (s != CG_OK) return s;
-    return cg_row_argmax_argmin(Z, plan->m, plan->d, imax, imin, stream);
 }

@@ -12,8 +12,12 @@ are functions of (seed, global row index), G of the seed alone.  Two layouts fol
   indices), and a coordinator keeps the largest / smallest, the lowest global index on
   ties (merge_anchor_records).
 
-The functions here are host logic (sharding, offsets, the collective, the merge); the
-per-rank compute is the library's (or, in the CPU tests, the oracle's).
+The helpers below are host logic (sharding, offsets, the collective, the merge);
+apply_csr_row_shard and nmf_anchors_column_shard are the library calls that run each
+rank's share on its GPU (cg_apply_csr, cg_nmf_anchors_csr) and combine the ranks.  The
+collectives move m x d floats (row shards) or m x 4 records (column shards) through
+whatever backend the process group has; CUDA results are staged through host memory, so
+a gloo group serves as well as NCCL.
 """
 from __future__ import annotations
 
@@ -93,3 +97,48 @@ def gather_anchor_records(rec: np.ndarray, group=None) -> list[np.ndarray]:
     out = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
     dist.all_gather(out, t, group=group)
     return [o.numpy() for o in out]
+
+
+def _host(t: torch.Tensor) -> torch.Tensor:
+    return t.detach().to("cpu", copy=True)
+
+
+def apply_csr_row_shard(row_ptr, col_idx, vals, d: int, m: int, B: int, seed: int, row_offset: int, group=None,
+                        **plan_options) -> torch.Tensor:
+    """T X for X sharded by rows over the ranks of `group`: this rank holds rows
+    [row_offset, row_offset + n_local) of X as CSR on its GPU (row_ptr local, starting at
+    0), computes T_p X_p = G (S_p X_p) with that global row offset (cg_apply_csr), and the
+    m x d outputs are summed over the group.  Every rank returns the whole T X (m x d fp32,
+    on the rank's device).  plan_options go to CountGauss (precision, scatter, ...)."""
+    from . import countgauss
+    n_local = int(row_ptr.numel()) - 1
+    plan = countgauss.CountGauss(n_local, d, m, B, seed, row_offset=row_offset, **plan_options)
+    Y = plan.apply_csr(row_ptr, col_idx, vals)
+    plan.check()
+    Yh = _host(Y)
+    sum_outputs(Yh, group)
+    return Yh.to(Y.device)
+
+
+def nmf_anchors_column_shard(row_ptr, col_idx, vals, d_local: int, m: int, B: int, seed: int, col_offset: int,
+                             group=None, **plan_options):
+    """Algorithm 1 step 3 for X sharded by columns (the data points of the paper's NMF
+    setting): this rank holds all n rows and columns [col_offset, col_offset + d_local) of
+    X (column indices local) as CSR on its GPU.  It computes its columns of Z = T X with
+    the per-row max / min (cg_nmf_anchors_csr), gathers every rank's (value, global column)
+    records and merges them, lowest global column on ties.  Returns (imax, imin), int64
+    numpy arrays of m global column indices, on every rank."""
+    from . import countgauss
+    n = int(row_ptr.numel()) - 1
+    if d_local > 0:
+        plan = countgauss.CountGauss(n, d_local, m, B, seed, **plan_options)
+        Z, jmax, jmin = plan.nmf_anchors(row_ptr, col_idx, vals)
+        plan.check()
+        Zh = _host(Z).numpy().astype(np.float64)
+        jmax = _host(jmax).numpy().astype(np.int64)
+        jmin = _host(jmin).numpy().astype(np.int64)
+        rows = np.arange(m)
+        rec = np.stack([Zh[rows, jmax], jmax + col_offset, Zh[rows, jmin], jmin + col_offset], axis=1)
+    else:
+        rec = np.full((m, 4), np.nan)
+    return merge_anchor_records(gather_anchor_records(rec, group))

@@ -129,6 +129,54 @@ def test_nmf_anchors_match_oracle():
     np.testing.assert_array_equal(imin.cpu().numpy()[clear_min], omin[clear_min])
 
 
+@pytest.mark.parametrize("d,m,precision", [(50, 24, "fp32"), (300, 5, "fp32"), (1500, 3, "fp32"), (64, 1, "fp32"),
+                                           (128, 128, "bf16"), (40, 9, "fp8")])
+def test_fused_anchors_against_row_argmax_and_oracle(d, m, precision):
+    """Algorithm 1 step 3 inside the split-K sum (one thread block per row of Z): Z within
+    fp32 rounding of cg_apply_csr's, imax / imin exactly the row argmax / argmin of that Z
+    (lowest index on ties), for rows of one to 47 column chunks and every contraction."""
+    n, B, seed = 6000, 1024, 29
+    X = synth.csr_bernoulli(n, d, 0.05, seed=4, values="uniform")
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).cuda()
+    ci = torch.from_numpy(X.col_idx).cuda()
+    v = torch.from_numpy(X.vals).cuda()
+    plan = cg().CountGauss(n, d, m, B, seed, precision=precision)
+    Z, imax, imin = plan.nmf_anchors(rp, ci, v)
+    Y = plan.apply_csr(rp, ci, v)
+    plan.check()
+    Zn = Z.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(Zn - Y.cpu().numpy()) <= 1e-6 * np.linalg.norm(Zn)
+    np.testing.assert_array_equal(imax.cpu().numpy(), np.argmax(Zn, axis=1))
+    np.testing.assert_array_equal(imin.cpu().numpy(), np.argmin(Zn, axis=1))
+    if precision == "fp32":
+        Zo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals)
+        assert np.linalg.norm(Zn - Zo) <= 1e-5 * np.linalg.norm(Zo)
+
+
+def test_fused_anchors_ties_take_lowest_column():
+    """Columns 5 and 17 of X equal, so columns 5 and 17 of Z are equal bit for bit (the
+    deterministic scatter's sums do not depend on order); the fused step 3 reports the
+    lower column wherever they hold a row's maximum or minimum."""
+    n, d, m, B, seed = 4000, 24, 32, 256, 31
+    Xd = synth.csr_bernoulli(n, d, 0.1, seed=5, values="uniform").to_dense()
+    Xd[:, 5] = 0.0
+    Xd[::3, 5] = 50.0  # large, so that column 5 often holds the max or the min
+    Xd[:, 17] = Xd[:, 5]
+    X = synth.csr_from_dense(Xd)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).cuda()
+    ci = torch.from_numpy(X.col_idx).cuda()
+    v = torch.from_numpy(X.vals).cuda()
+    plan = cg().CountGauss(n, d, m, B, seed, deterministic=True)
+    Z, imax, imin = plan.nmf_anchors(rp, ci, v)
+    plan.check()
+    Zn = Z.cpu().numpy()
+    np.testing.assert_array_equal(Zn[:, 5], Zn[:, 17])
+    im, jm = imax.cpu().numpy(), imin.cpu().numpy()
+    np.testing.assert_array_equal(im, np.argmax(Zn, axis=1))
+    np.testing.assert_array_equal(jm, np.argmin(Zn, axis=1))
+    assert (im == 5).sum() + (jm == 5).sum() > 0 and not ((im == 17).any() or (jm == 17).any())
+
+
 def test_argmax_ties_take_lowest_index():
     Z = torch.tensor([[1.0, 3.0, 3.0, -2.0, -2.0], [0.0, 0.0, 0.0, 0.0, 0.0]], device="cuda")
     imax, imin = cg().row_argmax_argmin(Z)
