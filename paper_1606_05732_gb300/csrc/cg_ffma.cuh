@@ -168,14 +168,23 @@ __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, 
         }
     }
     if (grp == 0) {
+        // 16-byte stores where the thread's TN columns are all in range and rows of `out`
+        // start 16-byte aligned
+        const bool vec = TN * tj + TN <= bn && (d & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(out) | ((n0 + TN * tj) * 4u)) & 15) == 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = m0 + 4 * ti + i;
             if (r >= m) continue;
+            float *o = out + static_cast<size_t>(r) * d + n0 + TN * tj;
+            if (vec) {
 #pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const int c = n0 + TN * tj + j;
-                if (TN * tj + j < bn) out[static_cast<size_t>(r) * d + c] = acc[i][j];
+                for (int j = 0; j < TN; j += 4)
+                    *reinterpret_cast<float4 *>(o + j) = make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    if (TN * tj + j < bn) o[j] = acc[i][j];
             }
         }
     }

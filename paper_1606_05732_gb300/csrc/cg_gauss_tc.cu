@@ -254,16 +254,26 @@ contract_tc_bf16_kernel(const float *__restrict__ SX, int m, int d, int64_t B, K
     const int row = quad * 32 + lane;
     const int grow = m0 + row;
     float *out = part + static_cast<size_t>(blockIdx.x) * m * d;
+    // whole 16-byte groups of a row when the tile is full and rows start 16-byte aligned
+    const bool vec = bn == NT && (d & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) | (n0 * 4u)) & 15) == 0;
     for (int c0 = grp * kCols; c0 < (grp + 1) * kCols; c0 += 32) {
         uint32_t r[32];
         tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(c0), r);
         tc::tmem_ld_wait();
         if (grow < m) {
+            float *o = out + static_cast<size_t>(grow) * d + n0 + c0;
+            const bool good = ok && issued > 0;
+            if (vec) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (c0 + j < bn)
-                    out[static_cast<size_t>(grow) * d + n0 + c0 + j] =
-                        (ok && issued > 0) ? __uint_as_float(r[j]) : 0.0f;
+                for (int j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4 *>(o + j) =
+                        good ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                           __uint_as_float(r[j + 3]))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < bn) o[j] = good ? __uint_as_float(r[j]) : 0.0f;
             }
         }
     }
@@ -521,11 +531,18 @@ contract_tc_fp8_kernel(const float *__restrict__ SX, int m, int d, int64_t B, Ke
     const bool ok = !abort_flag;
     const int grow = m0 + row;
     float *out = part + static_cast<size_t>(blockIdx.x) * m * d;
+    const bool vec = bn == NT && (d & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) | (n0 * 4u)) & 15) == 0;
     if (grow < m) {
+        float *o = out + static_cast<size_t>(grow) * d + n0 + half * (NT / 2);
+        if (vec) {
 #pragma unroll
-        for (int j = 0; j < NT / 2; ++j) {
-            const int c = half * (NT / 2) + j;
-            if (c < bn) out[static_cast<size_t>(grow) * d + n0 + c] = ok ? acc[j] : 0.0f;
+            for (int j = 0; j < NT / 2; j += 4)
+                *reinterpret_cast<float4 *>(o + j) = ok ? make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3])
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int j = 0; j < NT / 2; ++j)
+                if (half * (NT / 2) + j < bn) o[j] = ok ? acc[j] : 0.0f;
         }
     }
     tc::fence_before_sync();

@@ -58,8 +58,11 @@ __device__ __forceinline__ void hash_sign(Key k, uint64_t row, uint32_t B, uint3
     s = (w.y & 0x80000000u) ? -1.0f : 1.0f;
 }
 
+// u(w) = (2 (w >> 9) + 1) 2^-24, formed without an integer-to-float conversion: the float
+// with exponent 0 and mantissa w >> 9 is 1 + (w >> 9) 2^-23 exactly, and subtracting
+// 1 - 2^-24 is exact (the operands are within a factor of two), leaving (2 (w >> 9) + 1) 2^-24.
 __device__ __forceinline__ float uniform24(uint32_t w) {
-    return __uint2float_rn(((w >> 9) << 1) | 1u) * 5.9604644775390625e-8f;  // 2^-24
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.999999940395355224609375f;  // 1 - 2^-24
 }
 
 __device__ __forceinline__ float4 box_muller4(uint4 w) {
