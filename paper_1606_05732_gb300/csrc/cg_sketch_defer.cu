@@ -80,18 +80,38 @@ __device__ __forceinline__ bool stage_chunk(const int *__restrict__ row_ptr, int
     return true;
 }
 
+// Rows of a chunk whose nonzeros number at most kMapCap find a nonzero's row in a
+// per-warp map (one byte per nonzero, written by the row's lane: the rows are in order)
+// instead of by binary search over the row offsets.
+constexpr int kMapCap = 1024;
+
+// The row map of a staged chunk (after stage_chunk, end - beg <= kMapCap): lane l writes,
+// for each of its rows q = l + 32 r, q into s_map[k - beg] for the row's nonzeros k.
+template <int ROWS>
+__device__ __forceinline__ void map_rows(const int *s_rp, int beg, uint8_t *s_map) {
+    constexpr int R = ROWS / 32;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int q = r * 32 + lane;
+        const int a = s_rp[q], e = s_rp[q + 1];
+        for (int k = a; k < e; ++k) s_map[k - beg] = static_cast<uint8_t>(q);
+    }
+    __syncwarp();
+}
+
 // Pass 1 on one staged chunk: nonzeros of rows with h < bsplit are reduced into SX;
 // the others become records appended to records[rec_lo, rec_hi) through *s_count.
 // The nonzeros are swept 32 x kScatterUnroll at a time with coalesced evict-first
-// loads, each finding its row by a log2(ROWS)-step binary search over s_rp.  Bad
-// column indices, and records that would leave the region (only possible with
-// malformed offsets), are dropped and reported through `bad`.
+// loads, each finding its row in the row map (s_map non-null) or by a log2(ROWS)-step
+// binary search over s_rp.  Bad column indices, and records that would leave the region
+// (only possible with malformed offsets), are dropped and reported through `bad`.
 template <int ROWS>
 __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, const float *__restrict__ vals, int beg,
                                             int end, int d, float *__restrict__ SX, uint32_t bsplit,
                                             uint2 *__restrict__ records, int rec_lo, int rec_hi, int *s_count,
-                                            const int *s_rp, const uint32_t *s_h, const float *s_sg, uint64_t pol,
-                                            int &bad) {
+                                            const int *s_rp, const uint32_t *s_h, const float *s_sg,
+                                            const uint8_t *s_map, uint64_t pol, int &bad) {
     const int lane = threadIdx.x & 31;
     for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
         int col[kScatterUnroll];
@@ -115,9 +135,13 @@ __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, con
             float x = 0.0f;
             if (k < end) {
                 int lo = 0;
+                if (s_map != nullptr) {
+                    lo = s_map[k - beg];
+                } else {
 #pragma unroll
-                for (int step = ROWS / 2; step > 0; step >>= 1)
-                    if (s_rp[lo + step] <= k) lo += step;
+                    for (int step = ROWS / 2; step > 0; step >>= 1)
+                        if (s_rp[lo + step] <= k) lo += step;
+                }
                 const int j = col[u];
                 const uint32_t hb = s_h[lo];
                 if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
@@ -160,6 +184,7 @@ split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     __shared__ int s_rp[kWarps][ROWS + 1];
     __shared__ uint32_t s_h[kWarps][ROWS];
     __shared__ float s_sg[kWarps][ROWS];
+    __shared__ uint8_t s_map[kWarps][kMapCap];
     __shared__ int s_count;
     const int w = threadIdx.x >> 5;
     const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
@@ -180,9 +205,12 @@ split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     for (int first = r0 + w * ROWS; first < r1; first += kWarps * ROWS) {
         int beg, end;
         if (stage_chunk<ROWS>(row_ptr, first, r1, nnz, B, key, row_offset, s_rp[w], s_h[w], s_sg[w], pol, beg, end,
-                              bad))
+                              bad)) {
+            const bool mapped = end - beg <= kMapCap;  // warp-uniform
+            if (mapped) map_rows<ROWS>(s_rp[w], beg, s_map[w]);
             split_chunk<ROWS>(col_idx, vals, beg, end, d, SX, bsplit, records, rec_lo, rec_hi, &s_count, s_rp[w],
-                              s_h[w], s_sg[w], pol, bad);
+                              s_h[w], s_sg[w], mapped ? s_map[w] : nullptr, pol, bad);
+        }
     }
     if (bad) atomicOr(status, kStatusBounds);
     __syncthreads();
