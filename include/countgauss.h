@@ -201,13 +201,15 @@ CG_API cg_status cg_apply_csr(cg_plan *plan, const int32_t *row_ptr, const int32
 /* cg_apply_csr for a matrix of 2^31 nonzeros or more: the same transform (Section 1.1;
  * Algorithm 1 steps 1-2) with 64-bit row offsets, row_ptr int64[n+1] (device, 8-byte
  * aligned), col_idx int32[nnz], vals fp32[nnz], 0 <= nnz <= 2^40.  The scatter is the
- * one-pass atomic scatter (CG_OPT_SCATTER 0 or 1; CG_OPT_SCATTER_PASSES and
- * CG_OPT_SCATTER_ROWS apply), each warp chunk of rows taking its offsets relative to its
- * first nonzero.  Y (device, m x d) is overwritten.  Workspace:
+ * one-pass atomic scatter (CG_OPT_SCATTER 1; CG_OPT_SCATTER_PASSES and
+ * CG_OPT_SCATTER_ROWS apply) or the deferred scatter (CG_OPT_SCATTER 3, and automatic
+ * for an SX larger than 60 % of the L2, as in cg_apply_csr; the workspace then holds 8
+ * bytes per nonzero), each warp chunk of rows taking its offsets relative to its first
+ * nonzero.  Y (device, m x d) is overwritten.  Workspace:
  * cg_workspace_size(CG_OP_APPLY_CSR_I64, nnz).  Errors: CG_ERR_INVALID_ARG for null or
  * misaligned pointers or nnz out of range; CG_ERR_UNSUPPORTED with CG_OPT_DETERMINISTIC
- * = 1 or CG_OPT_SCATTER 2, 3 or 4.  Out-of-range column indices, out-of-range or decreasing
- * row offsets, and a chunk of rows (at most 128 consecutive rows) holding more than
+ * = 1 or CG_OPT_SCATTER 2 or 4.  Out-of-range column indices, out-of-range or decreasing
+ * row offsets, and a chunk of rows (at most 256 consecutive rows) holding more than
  * 2^31 - 2^20 stored entries are reported through the status word, the entries concerned
  * skipped. */
 CG_API cg_status cg_apply_csr_i64(cg_plan *plan, const int64_t *row_ptr, const int32_t *col_idx,
@@ -274,7 +276,8 @@ CG_API cg_status cg_sketch_dense(cg_plan *plan, const float *X, int64_t ldx, flo
 
 /* cg_sketch_csr for int64 row offsets (as cg_apply_csr_i64): SX = S.X, or SX += S.X with
  * CG_OPT_ACCUMULATE = 1, e.g. over row chunks of a stream, each with its CG_OPT_ROW_OFFSET.
- * Workspace: cg_workspace_size(CG_OP_SKETCH_I64, nnz) (the status word only).  Errors as
+ * Workspace: cg_workspace_size(CG_OP_SKETCH_I64, nnz) (the status word, and the deferred
+ * scatter's records when it runs).  Errors as
  * cg_apply_csr_i64, and CG_ERR_INVALID_ARG for an SX off a 16-byte boundary. */
 CG_API cg_status cg_sketch_csr_i64(cg_plan *plan, const int64_t *row_ptr, const int32_t *col_idx,
                                    const float *vals, int64_t nnz, float *SX,

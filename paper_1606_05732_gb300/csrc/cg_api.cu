@@ -266,6 +266,13 @@ size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
     return 0;
 }
 
+// Scratch bytes of the CSR scatter with int64 row offsets through plan p: the deferred
+// scatter's records, or none for the one-pass scatter.
+size_t scatter_scratch_i64(const cg_plan &p, int64_t nnz) {
+    if (!use_deferred(p, nnz)) return 0;
+    return sketch_deferred_scratch_bytes(nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas)));
+}
+
 // Workspace layout: [status 256 B][region A][region B][region C], each 256-aligned.
 // A: SX or W;  B: split-K partials;  C: scratch of the partitioned scatter.
 struct Layout {
@@ -327,8 +334,10 @@ Layout layout_for(const cg_plan &p, int op, int64_t nnz) {
         case CG_OP_APPLY_CSR_I64:
             L.a_bytes = sx;
             L.b_bytes = contract_partials_bytes(p);
+            L.c_bytes = scatter_scratch_i64(p, nnz);
             break;
         case CG_OP_SKETCH_I64:
+            L.c_bytes = scatter_scratch_i64(p, nnz);
             break;
         case CG_OP_APPLY_RIGHT_CSR:
             L.a_bytes = sx;
@@ -737,20 +746,26 @@ cg_status cg_apply_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_id
 }
 
 // Host-side checks of a CSR matrix with int64 row offsets and of the options its
-// scatter honours: the one-pass atomic scatter only (the deterministic, deferred and
-// partitioned scatters index with 32-bit offsets).
+// scatter honours: the one-pass atomic and the deferred scatters (the deterministic,
+// partitioned and binned scatters index with 32-bit offsets).
 cg_status check_csr_i64(const cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
                         int64_t nnz) {
     if (nnz < 0 || nnz > kMaxNnz64 || row_ptr == nullptr) return CG_ERR_INVALID_ARG;
     if (nnz > 0 && (col_idx == nullptr || vals == nullptr)) return CG_ERR_INVALID_ARG;
     if (misaligned(row_ptr, 8) || misaligned(col_idx, 4) || misaligned(vals, 4)) return CG_ERR_INVALID_ARG;
-    if (p->deterministic || p->scatter == 2 || p->scatter == 3 || p->scatter == 4) return CG_ERR_UNSUPPORTED;
+    if (p->deterministic || p->scatter == 2 || p->scatter == 4) return CG_ERR_UNSUPPORTED;
     return CG_OK;
 }
 
 // SX = S.X, or with clear = false SX += S.X, for int64 row offsets.
 cg_status run_sketch_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *col_idx, const float *vals,
-                             int64_t nnz, float *SX, void *ws, cudaStream_t st, bool clear) {
+                             int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st, bool clear) {
+    if (use_deferred(*p, nnz))
+        return from_cuda(launch_sketch_csr_deferred_i64(
+            reinterpret_cast<const long long *>(row_ptr), col_idx, vals, static_cast<int>(p->n), p->d,
+            static_cast<uint32_t>(p->B), static_cast<long long>(nnz), make_key(p->seed), p->row_offset, SX,
+            status_word(ws), region(ws, L.c_off), static_cast<int>(p->sketch_ctas), p->scatter_rows,
+            timing_pair(p, CG_KERNEL_SKETCH), st, clear));
     return from_cuda(launch_sketch_csr_atomic_i64(
         reinterpret_cast<const long long *>(row_ptr), col_idx, vals, static_cast<int>(p->n), p->d,
         static_cast<uint32_t>(p->B), static_cast<long long>(nnz), make_key(p->seed), p->row_offset, SX, status_word(ws),
@@ -768,7 +783,7 @@ cg_status cg_apply_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *co
     if ((s = check_ws(p, CG_OP_APPLY_CSR_I64, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
     float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
     cudaStream_t st = as_stream(stream);
-    if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, st, true)) != CG_OK) return s;
+    if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, L, st, true)) != CG_OK) return s;
     return run_contract(p, SX, Y, ws, L, st);
 }
 
@@ -800,7 +815,7 @@ cg_status cg_nmf_anchors_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32
     if ((s = check_ws(p, CG_OP_APPLY_CSR_I64, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
     float *SX = reinterpret_cast<float *>(region(ws, L.a_off));
     cudaStream_t st = as_stream(stream);
-    if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, st, true)) != CG_OK) return s;
+    if ((s = run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, L, st, true)) != CG_OK) return s;
     return run_contract(p, SX, Z, ws, L, st, false, imax, imin);
 }
 
@@ -812,7 +827,7 @@ cg_status cg_sketch_csr_i64(cg_plan *p, const int64_t *row_ptr, const int32_t *c
     if (s != CG_OK) return s;
     Layout L;
     if ((s = check_ws(p, CG_OP_SKETCH_I64, nnz, ws, ws_bytes, &L)) != CG_OK) return s;
-    return run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, as_stream(stream), !p->accumulate);
+    return run_sketch_csr_i64(p, row_ptr, col_idx, vals, nnz, SX, ws, L, as_stream(stream), !p->accumulate);
 }
 
 cg_status cg_apply_right_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,

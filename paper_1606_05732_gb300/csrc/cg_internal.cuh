@@ -147,6 +147,12 @@ cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, c
                                        uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                        void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
                                        bool clear = true);
+// The same with int64 row offsets (each warp chunk rebased to its first nonzero, record
+// indices and per-CTA counts 64-bit).
+cudaError_t launch_sketch_csr_deferred_i64(const long long *row_ptr, const int *col_idx, const float *vals, int n,
+                                           int d, uint32_t B, long long nnz, Key key, int64_t row_offset, float *SX,
+                                           int *status, void *scratch, int ctas, int rows, const EventPair *ev,
+                                           cudaStream_t stream, bool clear);
 
 // ---- binned scatter (cg_sketch_bin.cu) -----------------------------------------
 // Nonzeros binned by bucket range (slices of SX that fit in shared memory), each slice

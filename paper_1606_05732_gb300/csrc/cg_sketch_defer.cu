@@ -14,7 +14,10 @@
 //           which is then the one in L2.
 // Each half of SX is half the size, and the extra traffic is the records, 16 bytes per
 // deferred nonzero (written once, read once, with an evict-first L2 policy).  Sums are
-// fp32 in an order that depends on timing, as with the atomic scatter.
+// fp32 in an order that depends on timing, as with the atomic scatter.  Both passes are
+// templated on the type of the row offsets: int, or long long for matrices of 2^31
+// nonzeros or more (warp chunks rebased to their first nonzero, 64-bit record indices
+// and per-CTA counts).
 #include "cg_internal.cuh"
 #include "cg_scatter.cuh"
 
@@ -36,25 +39,58 @@ __device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p, uint64_t pol) {
     return v;
 }
 
+// Shared-memory counter of a CTA's records: returns the old value.
+__device__ __forceinline__ int add_count(int *c, int v) { return atomicAdd(c, v); }
+__device__ __forceinline__ long long add_count(long long *c, int v) {
+    return static_cast<long long>(atomicAdd(reinterpret_cast<unsigned long long *>(c), static_cast<unsigned long long>(v)));
+}
+
 // Rows [first, min(first + ROWS, n)) staged as in scatter_chunk: lane l loads the
 // row_ptr entries of rows first + l + 32 r and hashes those rows into s_rp[ROWS + 1],
-// s_h[ROWS], s_sg[ROWS].  Returns the chunk's nonzero range [beg, end), or false
-// (setting `bad`) if the offsets leave [0, nnz] or are out of order.  All lanes of
-// the warp take part.
-template <int ROWS>
-__device__ __forceinline__ bool stage_chunk(const int *__restrict__ row_ptr, int first, int n, int nnz, uint32_t B,
+// s_h[ROWS], s_sg[ROWS].  RP is the type of the row offsets: int, or long long for
+// matrices of 2^31 nonzeros or more, whose chunk offsets are rebased to the chunk's first
+// nonzero `base` (so s_rp holds 32-bit offsets; a chunk of more than kMaxChunkNnz
+// nonzeros is malformed); with int, base = 0.  Returns the chunk's nonzero range
+// [beg, end) relative to base, or false (setting `bad`) if the offsets leave [0, nnz] or
+// are out of order.  All lanes of the warp take part.
+template <int ROWS, typename RP>
+__device__ __forceinline__ bool stage_chunk(const RP *__restrict__ row_ptr, int first, int n, RP nnz, uint32_t B,
                                             Key key, int64_t row_offset, int *s_rp, uint32_t *s_h, float *s_sg,
-                                            uint64_t pol, int &beg, int &end, int &bad) {
+                                            uint64_t pol, int &beg, int &end, RP &base, int &bad) {
     static_assert(ROWS == 32 || ROWS == 64 || ROWS == 128 || ROWS == 256, "chunk height");
     constexpr int R = ROWS / 32;
     const int lane = threadIdx.x & 31;
     const int last = min(first + ROWS, n);
-    end = __ldg(row_ptr + last);
     int rp[R];
+    bool malformed = false;
+    if constexpr (sizeof(RP) == 4) {
+        base = 0;
+        end = __ldg(row_ptr + last);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {  // all row_ptr loads in flight before the hashing
-        const int i = first + r * 32 + lane;
-        rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
+        for (int r = 0; r < R; ++r) {  // all row_ptr loads in flight before the hashing
+            const int i = first + r * 32 + lane;
+            rp[r] = i < n ? ld_stream_i32(row_ptr + i, pol) : end;
+        }
+        malformed = end > nnz;
+    } else {
+        const long long end64 = __ldg(row_ptr + last);
+        long long rp64[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = first + r * 32 + lane;
+            rp64[r] = i < n ? ld_stream_i64(row_ptr + i, pol) : end64;
+        }
+        base = __shfl_sync(0xffffffffu, rp64[0], 0);  // row_ptr[first]
+        malformed = base < 0 || end64 > nnz || end64 < base || end64 - base > kMaxChunkNnz;
+        const long long span = malformed ? 0 : end64 - base;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long rel = rp64[r] - base;
+            rp[r] = rel >= 0 && rel <= span ? static_cast<int>(rel) : -1;  // -1 breaks the order check
+            malformed |= rel < 0 || rel > span;
+        }
+        malformed = __any_sync(0xffffffffu, malformed);
+        end = static_cast<int>(span);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -72,7 +108,7 @@ __device__ __forceinline__ bool stage_chunk(const int *__restrict__ row_ptr, int
     bool ordered = true;
 #pragma unroll
     for (int r = 0; r < R; ++r) ordered &= s_rp[r * 32 + lane] <= s_rp[r * 32 + lane + 1];
-    if (beg < 0 || end > nnz || !__all_sync(0xffffffffu, ordered)) {  // malformed row_ptr: skip the chunk
+    if (malformed || beg < 0 || !__all_sync(0xffffffffu, ordered)) {  // malformed row_ptr: skip the chunk
         bad = 1;
         __syncwarp();
         return false;
@@ -101,17 +137,19 @@ __device__ __forceinline__ void map_rows(const int *s_rp, int beg, uint8_t *s_ma
 }
 
 // Pass 1 on one staged chunk: nonzeros of rows with h < bsplit are reduced into SX;
-// the others become records appended to records[rec_lo, rec_hi) through *s_count.
-// The nonzeros are swept 32 x kScatterUnroll at a time with coalesced evict-first
-// loads, each finding its row in the row map (s_map non-null) or by a log2(ROWS)-step
-// binary search over s_rp.  Bad column indices, and records that would leave the region
-// (only possible with malformed offsets), are dropped and reported through `bad`.
-template <int ROWS>
+// the others become records appended to the CTA's region region[0, cap) through
+// *s_count.  col_idx and vals point at the chunk's base nonzero, so nonzero k of
+// [beg, end) is col_idx[k], vals[k].  The nonzeros are swept 32 x kScatterUnroll at a
+// time with coalesced evict-first loads, each finding its row in the row map (s_map
+// non-null) or by a log2(ROWS)-step binary search over s_rp.  Bad column indices, and
+// records that would leave the region (only possible with malformed offsets), are
+// dropped and reported through `bad`.
+template <int ROWS, typename RP>
 __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, const float *__restrict__ vals, int beg,
                                             int end, int d, float *__restrict__ SX, uint32_t bsplit,
-                                            uint2 *__restrict__ records, int rec_lo, int rec_hi, int *s_count,
-                                            const int *s_rp, const uint32_t *s_h, const float *s_sg,
-                                            const uint8_t *s_map, uint64_t pol, int &bad) {
+                                            uint2 *__restrict__ region, RP cap, RP *s_count, const int *s_rp,
+                                            const uint32_t *s_h, const float *s_sg, const uint8_t *s_map,
+                                            uint64_t pol, int &bad) {
     const int lane = threadIdx.x & 31;
     for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
         int col[kScatterUnroll];
@@ -157,13 +195,13 @@ __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, con
             }
             const unsigned mask = __ballot_sync(0xffffffffu, defer);
             if (mask == 0u) continue;  // warp-uniform
-            int base = 0;
-            if (lane == 0) base = atomicAdd(s_count, __popc(mask));
+            RP base = 0;
+            if (lane == 0) base = add_count(s_count, __popc(mask));
             base = __shfl_sync(0xffffffffu, base, 0);
             if (defer) {
-                const int at = rec_lo + base + __popc(mask & ((1u << lane) - 1u));
-                if (at < rec_hi)
-                    st_stream_u2(records + at, make_uint2(cell, __float_as_uint(x)), pol);
+                const RP at = base + __popc(mask & ((1u << lane) - 1u));
+                if (at < cap)
+                    st_stream_u2(region + at, make_uint2(cell, __float_as_uint(x)), pol);
                 else
                     bad = 1;
             }
@@ -175,22 +213,22 @@ __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, con
 // Pass 1: CTA c takes rows [c R, min((c+1) R, n)) (R a multiple of ROWS) and the
 // record slots row_ptr[c R] .. row_ptr[min((c+1) R, n)] - 1; it writes how many records
 // it made to counts[c] (0 for a CTA whose region offsets are malformed).
-template <int ROWS>
+template <int ROWS, typename RP>
 __global__ void __launch_bounds__(kThreads)
-split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
-                  int n, int d, uint32_t B, int nnz, Key key, int64_t row_offset, float *__restrict__ SX,
-                  uint32_t bsplit, int rows_per_cta, uint2 *__restrict__ records, int *__restrict__ counts,
+split_pass_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
+                  int n, int d, uint32_t B, RP nnz, Key key, int64_t row_offset, float *__restrict__ SX,
+                  uint32_t bsplit, int rows_per_cta, uint2 *__restrict__ records, RP *__restrict__ counts,
                   int *__restrict__ status) {
     __shared__ int s_rp[kWarps][ROWS + 1];
     __shared__ uint32_t s_h[kWarps][ROWS];
     __shared__ float s_sg[kWarps][ROWS];
     __shared__ uint8_t s_map[kWarps][kMapCap];
-    __shared__ int s_count;
+    __shared__ RP s_count;
     const int w = threadIdx.x >> 5;
     const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
     const int r1 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(r0) + rows_per_cta));
-    const int rec_lo = __ldg(row_ptr + r0);
-    const int rec_hi = __ldg(row_ptr + r1);
+    const RP rec_lo = __ldg(row_ptr + r0);
+    const RP rec_hi = __ldg(row_ptr + r1);
     if (rec_lo < 0 || rec_hi > nnz || rec_lo > rec_hi) {  // uniform over the CTA
         if (threadIdx.x == 0) {
             counts[blockIdx.x] = 0;
@@ -204,12 +242,14 @@ split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
     int bad = 0;
     for (int first = r0 + w * ROWS; first < r1; first += kWarps * ROWS) {
         int beg, end;
-        if (stage_chunk<ROWS>(row_ptr, first, r1, nnz, B, key, row_offset, s_rp[w], s_h[w], s_sg[w], pol, beg, end,
-                              bad)) {
+        RP base;
+        if (stage_chunk<ROWS, RP>(row_ptr, first, r1, nnz, B, key, row_offset, s_rp[w], s_h[w], s_sg[w], pol, beg,
+                                  end, base, bad)) {
             const bool mapped = end - beg <= kMapCap;  // warp-uniform
             if (mapped) map_rows<ROWS>(s_rp[w], beg, s_map[w]);
-            split_chunk<ROWS>(col_idx, vals, beg, end, d, SX, bsplit, records, rec_lo, rec_hi, &s_count, s_rp[w],
-                              s_h[w], s_sg[w], mapped ? s_map[w] : nullptr, pol, bad);
+            split_chunk<ROWS, RP>(col_idx + base, vals + base, beg, end, d, SX, bsplit, records + rec_lo,
+                                  rec_hi - rec_lo, &s_count, s_rp[w], s_h[w], s_sg[w], mapped ? s_map[w] : nullptr,
+                                  pol, bad);
         }
     }
     if (bad) atomicOr(status, kStatusBounds);
@@ -221,9 +261,10 @@ split_pass_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_i
 // for its share of the upper half of SX (cells [lo_cell, cells)) to be brought into L2,
 // where pass 1 left the lower half (a small gain: at the ladder size the pass is bound by
 // the issue of its random reductions, not by their L2 misses).
+template <typename RP>
 __global__ void __launch_bounds__(kThreads)
-replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, const uint2 *__restrict__ records,
-                      const int *__restrict__ counts, uint32_t lo_cell, uint32_t cells, float *__restrict__ SX) {
+replay_records_kernel(const RP *__restrict__ row_ptr, int n, int rows_per_cta, const uint2 *__restrict__ records,
+                      const RP *__restrict__ counts, uint32_t lo_cell, uint32_t cells, float *__restrict__ SX) {
     if (threadIdx.x == 0 && cells > lo_cell) {
         const uint64_t share = (static_cast<uint64_t>(cells - lo_cell) + gridDim.x - 1) / gridDim.x;
         const uint64_t c0 = lo_cell + share * blockIdx.x;
@@ -239,14 +280,14 @@ replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, 
     }
     const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
     const int r1 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(r0) + rows_per_cta));
-    const int start = __ldg(row_ptr + r0);
+    const RP start = __ldg(row_ptr + r0);
     // records were written only inside [row_ptr[r0], row_ptr[r1]) (pass 1 set counts to 0
     // where these offsets were malformed)
-    const int cnt = min(counts[blockIdx.x], __ldg(row_ptr + r1) - start);
+    const RP cnt = min(counts[blockIdx.x], __ldg(row_ptr + r1) - start);
     if (cnt <= 0) return;
     const uint64_t pol = l2_evict_first_policy();
     constexpr int kInFlight = 4;  // record loads in flight per thread before their reductions
-    int i = threadIdx.x;
+    RP i = threadIdx.x;
     for (; i + (kInFlight - 1) * kThreads < cnt; i += kInFlight * kThreads) {
         uint2 r[kInFlight];
 #pragma unroll
@@ -264,7 +305,7 @@ replay_records_kernel(const int *__restrict__ row_ptr, int n, int rows_per_cta, 
 // Chunk height of pass 1: as for the one-pass scatter (about 96 nonzeros per chunk), but
 // 256 rows for rows of under 1.5 nonzeros: eight independent hashes per lane and fewer
 // chunk boundaries (at 1.28 nonzeros per row, 0.976 ms against 1.010 ms with 128 rows).
-int staged_rows(int n, int nnz, int forced) {
+int staged_rows(int n, int64_t nnz, int forced) {
     if (forced == 32 || forced == 64 || forced == 128 || forced == 256) return forced;
     const double per_row = n > 0 ? static_cast<double>(nnz) / n : 0.0;
     if (per_row * 32 >= 96.0) return 32;
@@ -278,15 +319,17 @@ int staged_rows(int n, int nnz, int forced) {
 bool deferred_supported(int64_t B, int d) { return static_cast<uint64_t>(B) * static_cast<uint64_t>(d) < (1ull << 32); }
 
 size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas) {
-    return align256(static_cast<size_t>(nnz) * sizeof(uint2)) + align256(static_cast<size_t>(ctas) * sizeof(int));
+    return align256(static_cast<size_t>(nnz) * sizeof(uint2)) + align256(static_cast<size_t>(ctas) * sizeof(long long));
 }
 
 int sketch_deferred_ctas(int ctas) { return ctas > 0 ? ctas : sketch_default_ctas(); }
 
-cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
-                                       uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
-                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
-                                       bool clear) {
+namespace {
+
+template <typename RP>
+cudaError_t sketch_deferred(const RP *row_ptr, const int *col_idx, const float *vals, int n, int d, uint32_t B,
+                            RP nnz, Key key, int64_t row_offset, float *SX, int *status, void *scratch, int ctas,
+                            int rows, const EventPair *ev, cudaStream_t stream, bool clear) {
     cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
     if (e != cudaSuccess || n == 0) return e;
     const int G = sketch_deferred_ctas(ctas);
@@ -295,32 +338,54 @@ cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, c
     const int rows_per_cta = (per + H - 1) / H * H;
     const int used = (n + rows_per_cta - 1) / rows_per_cta;
     uint2 *records = static_cast<uint2 *>(scratch);
-    int *counts = reinterpret_cast<int *>(static_cast<char *>(scratch) + align256(static_cast<size_t>(nnz) * sizeof(uint2)));
+    RP *counts = reinterpret_cast<RP *>(static_cast<char *>(scratch) + align256(static_cast<size_t>(nnz) * sizeof(uint2)));
     const uint32_t bsplit = B / 2;
     record(ev, true, stream);
     switch (H) {
         case 256:
-            split_pass_kernel<256><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                                  SX, bsplit, rows_per_cta, records, counts, status);
+            split_pass_kernel<256, RP><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                      row_offset, SX, bsplit, rows_per_cta, records,
+                                                                      counts, status);
             break;
         case 128:
-            split_pass_kernel<128><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                                  SX, bsplit, rows_per_cta, records, counts, status);
+            split_pass_kernel<128, RP><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                      row_offset, SX, bsplit, rows_per_cta, records,
+                                                                      counts, status);
             break;
         case 64:
-            split_pass_kernel<64><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                                 SX, bsplit, rows_per_cta, records, counts, status);
+            split_pass_kernel<64, RP><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                     row_offset, SX, bsplit, rows_per_cta, records,
+                                                                     counts, status);
             break;
         default:
-            split_pass_kernel<32><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
-                                                                 SX, bsplit, rows_per_cta, records, counts, status);
+            split_pass_kernel<32, RP><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                     row_offset, SX, bsplit, rows_per_cta, records,
+                                                                     counts, status);
             break;
     }
-    replay_records_kernel<<<used, kThreads, 0, stream>>>(row_ptr, n, rows_per_cta, records, counts,
-                                                         bsplit * static_cast<uint32_t>(d),
-                                                         B * static_cast<uint32_t>(d), SX);
+    replay_records_kernel<RP><<<used, kThreads, 0, stream>>>(row_ptr, n, rows_per_cta, records, counts,
+                                                             bsplit * static_cast<uint32_t>(d),
+                                                             B * static_cast<uint32_t>(d), SX);
     record(ev, false, stream);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
+                                       uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
+                                       void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
+                                       bool clear) {
+    return sketch_deferred<int>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, status, scratch, ctas, rows,
+                                ev, stream, clear);
+}
+
+cudaError_t launch_sketch_csr_deferred_i64(const long long *row_ptr, const int *col_idx, const float *vals, int n,
+                                           int d, uint32_t B, long long nnz, Key key, int64_t row_offset, float *SX,
+                                           int *status, void *scratch, int ctas, int rows, const EventPair *ev,
+                                           cudaStream_t stream, bool clear) {
+    return sketch_deferred<long long>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, status, scratch, ctas,
+                                      rows, ev, stream, clear);
 }
 
 }  // namespace cg

@@ -140,8 +140,8 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
     assert lib.cg_apply_csr_i64(h, P((1 << 20) + 4), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1  # 4-aligned
     assert lib.cg_apply_csr_i64(h, fake, P(0), fake, 10, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
-    # the deterministic, deferred, partitioned and binned scatters take 32-bit offsets only
-    for opt, val in ((2, 1), (7, 3), (7, 2), (7, 4)):
+    # the deterministic, partitioned and binned scatters take 32-bit offsets only
+    for opt, val in ((2, 1), (7, 2), (7, 4)):
         assert lib.cg_plan_set_option(h, opt, val) == 0
         assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 1 << 30, P(0)) == 2
         assert lib.cg_plan_set_option(h, opt, 0) == 0
@@ -162,11 +162,20 @@ def test_wide_offsets_argument_errors_launch_nothing(lib):
     assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, 10, P(0), fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_adjoint_i64(h, P(0), fake, fake, 10, fake, fake, 1 << 30, P(0)) == 1
     assert lib.cg_apply_adjoint_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
-    # workspace: SX and the split-K partials, no scatter scratch, whatever nnz
+    # workspace: SX and the split-K partials, no scatter scratch (one-pass scatter), whatever nnz
     sz2 = ctypes.c_size_t()
     assert lib.cg_workspace_size(h, 9, 10, ctypes.byref(sz)) == 0
     assert lib.cg_workspace_size(h, 9, 1 << 33, ctypes.byref(sz2)) == 0
     assert sz.value == sz2.value >= 256 + 16 * 4 * 4
+    # the deferred scatter (CG_OPT_SCATTER = 3) adds its 8-byte records, one slot per nonzero
+    assert lib.cg_plan_set_option(h, 7, 3) == 0
+    sz3, sz4 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.cg_workspace_size(h, 9, 1 << 33, ctypes.byref(sz3)) == 0
+    assert lib.cg_workspace_size(h, 10, 1 << 33, ctypes.byref(sz4)) == 0
+    assert sz3.value - sz2.value >= 8 << 33 and sz3.value - sz2.value < (8 << 33) + (1 << 20)
+    assert sz4.value >= 256 + (8 << 33)
+    assert lib.cg_apply_csr_i64(h, fake, fake, fake, 10, fake, fake, 16, P(0)) == 3
+    assert lib.cg_plan_set_option(h, 7, 0) == 0
     lib.cg_plan_destroy(h)
 
 

@@ -3,9 +3,10 @@ Algorithm 1 steps 1-2) and its adjoint at the stored entries, for CSR matrices g
 64-bit row offsets, i.e. of 2^31 nonzeros or more.
 
 Parity with the FP64 oracle at sizes it finishes in seconds (several chunks of rows and
-a ragged tail, every chunk height); at 2.4e9 nonzeros (past 2^31), agreement with the
-32-bit path applied to row blocks with their global row offsets, which is the same
-transform by linearity (h and sigma depend on the global row index only).  Malformed
+a ragged tail, every chunk height), for the one-pass and the deferred scatter; past 2^31
+nonzeros (2.3e9 and 2.4e9), agreement with the 32-bit path applied to row blocks with
+their global row offsets, which is the same transform by linearity (h and sigma depend
+on the global row index only), and sampled rows of SX against their definition.  Malformed
 offsets are reported through the status word and skipped.  Bar: relative Frobenius
 error 1e-5 (FP32); the adjoint's values are the same arithmetic as the 32-bit path's, so
 the two agree bit for bit.
@@ -85,13 +86,42 @@ def test_same_as_32_bit_offsets():
     assert rel(Y64, Y32) < FP32_TOL
 
 
-@pytest.mark.parametrize("rows", [1, 32, 128])
-def test_malformed_offsets_are_reported(rows):
+@pytest.mark.parametrize("rows", [0, 32, 64, 128, 256])
+@pytest.mark.parametrize("n,d,m,B,seed,per_row", [(70001, 37, 13, 3001, 51, 6), (4099, 64, 32, 512, 52, 64),
+                                                  (100_000, 16, 8, 4096, 53, 1)])
+def test_deferred_parity_with_oracle(n, d, m, B, seed, per_row, rows):
+    """The deferred scatter (CG_OPT_SCATTER = 3) with int64 offsets: ragged rows (empty
+    ones, full ones), every chunk height, a row offset; Y and SX against the oracle, and SX
+    accumulated over two row blocks (each with its global row offset) equal to the whole."""
+    X = synth.csr_ragged(n, d, seed=seed, max_row=per_row)
+    rp, ci, v = dev_csr64(X)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="deferred", scatter_rows=rows, row_offset=777)
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=777, return_sx=True)
+    assert rel(Y, Yo) < FP32_TOL
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    assert rel(SX, SXo) < FP32_TOL
+    cut = n // 3
+    k0 = int(X.row_ptr[cut])
+    a = cg().CountGauss(cut, d, m, B, seed, scatter="deferred", scatter_rows=rows, row_offset=777)
+    b = cg().CountGauss(n - cut, d, m, B, seed, scatter="deferred", scatter_rows=rows, row_offset=777 + cut)
+    SXa = a.sketch_csr(rp[:cut + 1].contiguous(), ci[:k0], v[:k0])
+    b.sketch_csr((rp[cut:] - k0).contiguous(), ci[k0:], v[k0:], out=SXa, accumulate=True)
+    a.check()
+    b.check()
+    assert rel(SXa.cpu().numpy(), SXo) < FP32_TOL
+
+
+@pytest.mark.parametrize("scatter,rows", [("auto", 1), ("auto", 32), ("auto", 128), ("deferred", 0),
+                                          ("deferred", 32), ("deferred", 256)])
+def test_malformed_offsets_are_reported(scatter, rows):
     from paper_1606_05732_gb300 import _lib
     n, d, m, B, seed = 20_000, 16, 8, 1024, 36
     X = synth.csr_ragged(n, d, seed=7, max_row=4)
     rp, ci, v = dev_csr64(X)
-    plan = cg().CountGauss(n, d, m, B, seed, scatter_rows=rows)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter=scatter, scatter_rows=rows)
     bad = rp.clone()
     bad[n // 2], bad[n // 2 + 1] = rp[n // 2 + 1].item() + 1, rp[n // 2].item()  # decreasing
     plan.apply_csr(bad, ci, v)
@@ -131,6 +161,58 @@ def test_past_2_pow_31_nonzeros_matches_row_blocks():
         Yb += part.apply_csr((rp[r0:r1 + 1] - k0).int(), ci[k0:k1], v[k0:k1])
         part.check()
     assert rel(Y.cpu().numpy(), Yb.cpu().numpy()) < FP32_TOL
+
+
+def test_deferred_past_2_pow_31_nonzeros_matches_row_blocks_and_oracle():
+    """2^24 rows x 128 columns with 136 nonzeros per row on average (about 2.3e9 nonzeros,
+    18 GB of CSR) into an SX of 2^18 x 128 (128 MB, past the L2): the automatic choice is
+    the deferred scatter with int64 offsets (its workspace holds 8 bytes per nonzero).  Y
+    equals the sum of the 32-bit path over two row blocks; SX at 64 sampled buckets, half
+    of them at or above B/2 (the rows reduced by the replay pass), equals the definition
+    (sum of sigma(i) X[i, :] over the rows with h(i) = b, h and sigma from the oracle) in
+    FP64."""
+    from paper_1606_05732_gb300 import _lib
+    n, d, m, B, seed = 1 << 24, 128, 32, 1 << 18, 38
+    rp, ci, v = synth.wide_csr_device(n, d, 136, seed)
+    nnz = ci.numel()
+    assert nnz > (1 << 31)
+    plan = cg().CountGauss(n, d, m, B, seed)
+    assert plan.workspace_size(_lib.OP_APPLY_CSR_I64, nnz) >= 8 * nnz
+    Y = plan.apply_csr(rp, ci, v)
+    plan.check()
+    Yb = torch.zeros_like(Y)
+    cut = n // 2
+    for r0, r1 in ((0, cut), (cut, n)):
+        k0, k1 = int(rp[r0].item()), int(rp[r1].item())
+        part = cg().CountGauss(r1 - r0, d, m, B, seed, row_offset=r0)
+        Yb += part.apply_csr((rp[r0:r1 + 1] - k0).int(), ci[k0:k1], v[k0:k1])
+        part.check()
+        del part
+    assert rel(Y.cpu().numpy(), Yb.cpu().numpy()) < FP32_TOL
+
+    SX = plan.sketch_csr(rp, ci, v)
+    plan.check()
+    rng = np.random.default_rng(seed)
+    sample = np.concatenate([rng.choice(B // 2, 32, replace=False),
+                             B // 2 + rng.choice(B // 2, 32, replace=False)]).astype(np.int64)
+    h, sg = oracle.hash_sign(seed, B, 0, n)
+    rows = np.nonzero(np.isin(h, sample))[0]
+    rows_d = torch.from_numpy(rows).cuda()
+    starts = rp[rows_d]
+    lens = rp[rows_d + 1] - starts
+    total = int(lens.sum().item())
+    first = torch.cumsum(lens, 0) - lens
+    idx = torch.arange(total, device="cuda") - torch.repeat_interleave(first - starts, lens)
+    cols = ci[idx].cpu().numpy().astype(np.int64)
+    xs = v[idx].cpu().numpy().astype(np.float64)
+    owner = np.repeat(rows, lens.cpu().numpy())
+    sample = np.sort(sample)
+    E = np.zeros((sample.size, d), np.float64)
+    np.add.at(E, (np.searchsorted(sample, h[owner]), cols), sg[owner] * xs)
+    assert np.count_nonzero(E) > 0
+    assert rel(SX[torch.from_numpy(sample).cuda()].cpu().numpy(), E) < FP32_TOL
+    del plan, SX, Y, Yb, rp, ci, v
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("n,d,m,B,seed,per_row", [(70001, 37, 13, 3001, 41, 6), (4099, 64, 32, 512, 42, 64)])
