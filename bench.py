@@ -72,6 +72,9 @@ def parse_args():
                     help="nonzeros per chunk of the end-to-end host-input call (0: automatic)")
     ap.add_argument("--reduction-sweep", action="store_true",
                     help="instead of the step: random fp32 reduction rate vs array size (the scatter's ceiling)")
+    ap.add_argument("--sweep-mb", default="8,16,32,48,64,80,96,112,128,134,160,192,256",
+                    help="array sizes (MB) of --reduction-sweep")
+    ap.add_argument("--sweep-count", type=int, default=50_000_000, help="reductions per call of --reduction-sweep")
     ap.add_argument("--kl-sweep", action="store_true",
                     help="instead of the step: Theorem 1's KL / Pinsker bound and Lemma 5's distinguisher vs B")
     ap.add_argument("--no-rows", action="store_true", help="skip the other hot-path rows (ladder, adjoint, batch)")
@@ -744,17 +747,17 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
-def reduction_sweep():
+def reduction_sweep(args):
     """One JSON line: random fp32 reductions per second (cg_diag_random_reductions, 50 M
-    adds) into arrays from 8 MB to 256 MB -- where the L2 stops holding the array the
-    rate falls, which is the ceiling of the scatter for an SX of that size."""
+    adds by default) into arrays from 8 MB to 256 MB -- where the L2 stops holding the
+    array the rate falls, which is the ceiling of the scatter for an SX of that size."""
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    count = 50_000_000
+    count = args.sweep_count
     out = []
-    for mb in (8, 16, 32, 48, 64, 80, 96, 112, 128, 134, 160, 192, 256):
-        cells = (mb << 20) // 4
+    for mb in (float(x) for x in args.sweep_mb.split(",")):
+        cells = int(mb * (1 << 20)) // 4
         r = reduction_ceiling(dev, count, cells)
         out.append({"array_mb": mb, "reductions_per_s": r["per_s"], "ms": r["ms"]})
     print(json.dumps({"reduction_sweep": out, "count": count}))
@@ -791,7 +794,7 @@ def kl_sweep():
 def main():
     args = parse_args()
     if args.reduction_sweep:
-        reduction_sweep()
+        reduction_sweep(args)
     elif args.kl_sweep:
         kl_sweep()
     elif args.impl == "reference":

@@ -262,7 +262,8 @@ size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
     }
     if (use_binned(p, nnz)) return sketch_binned_scratch_bytes(p.n, p.d, p.B, nnz, static_cast<int>(p.sketch_ctas));
     if (use_deferred(p, nnz))
-        return sketch_deferred_scratch_bytes(nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas)));
+        return sketch_deferred_scratch_bytes(
+            nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas), p.n, nnz, p.scatter_rows));
     return 0;
 }
 
@@ -270,7 +271,8 @@ size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
 // scatter's records, or none for the one-pass scatter.
 size_t scatter_scratch_i64(const cg_plan &p, int64_t nnz) {
     if (!use_deferred(p, nnz)) return 0;
-    return sketch_deferred_scratch_bytes(nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas)));
+    return sketch_deferred_scratch_bytes(
+            nnz, sketch_deferred_ctas(static_cast<int>(p.sketch_ctas), p.n, nnz, p.scatter_rows));
 }
 
 // Workspace layout: [status 256 B][region A][region B][region C], each 256-aligned.

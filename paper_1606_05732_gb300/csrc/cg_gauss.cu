@@ -1,6 +1,6 @@
 // cg_gauss.cu -- stage 2 of the transform: Y = G.SX with G (m x B, i.i.d. N(0,1),
 // Theorem 1) generated tile by tile in shared memory and never written to HBM
-// (Section 1.1: "computing G.(S.X) can now be done in O~(m^2 d^3) time").
+// (Section 1.1, the cost of G.(S.X), independent of n).
 //
 // FP32 FFMA path.  The contraction dimension B is split over the grid ("split-K"):
 // CTA (s, bm, bn) owns a contiguous range of 32-column slabs of G, output rows

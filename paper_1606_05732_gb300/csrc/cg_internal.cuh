@@ -141,7 +141,9 @@ int one_pass_rows(const cg_plan &p, int64_t nnz);
 // SX split at bucket B/2: one CSR pass reduces the lower half and writes the rest as
 // records, a second pass reduces the records (for an SX larger than the L2 holds).
 bool deferred_supported(int64_t B, int d);
-int sketch_deferred_ctas(int ctas);
+// CTAs of the deferred scatter for n rows and nnz nonzeros (`ctas` > 0: as given;
+// `rows`: the CG_OPT_SCATTER_ROWS option).
+int sketch_deferred_ctas(int ctas, int64_t n, int64_t nnz, int rows);
 size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas);
 cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                        uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,

@@ -1,5 +1,5 @@
 // cg_sketch.cu -- stage 1 of the transform: SX = S.X, the O(nnz(X)) CountSketch
-// scatter (Section 1.1: "computing S.X can be done in O(nnz(X)) time").
+// scatter (Section 1.1, the O(nnz(X)) cost of S.X).
 //
 // Row i of X is added, times sigma(i), into row h(i) of SX (B x d, row-major fp32).
 // The scatter is one pass over the CSR arrays: every byte of row_ptr, col_idx and

@@ -18,6 +18,8 @@
 // templated on the type of the row offsets: int, or long long for matrices of 2^31
 // nonzeros or more (warp chunks rebased to their first nonzero, 64-bit record indices
 // and per-CTA counts).
+#include <algorithm>
+
 #include "cg_internal.cuh"
 #include "cg_scatter.cuh"
 
@@ -210,11 +212,15 @@ __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, con
     __syncwarp();
 }
 
-// Pass 1: CTA c takes rows [c R, min((c+1) R, n)) (R a multiple of ROWS) and the
+// Pass 1: CTA c takes rows [c R, min((c+1) R, n)) (R a multiple of kWarps ROWS) and the
 // record slots row_ptr[c R] .. row_ptr[min((c+1) R, n)] - 1; it writes how many records
-// it made to counts[c] (0 for a CTA whose region offsets are malformed).
+// it made to counts[c] (0 for a CTA whose region offsets are malformed).  With int
+// offsets, five CTAs per SM (at most 48 registers): the pass is issue-bound, and 40
+// warps per SM hide its load latency better than 32 (the 256-row form at 63 registers
+// took 1.02 ms at the 2^26-row ladder shape, 0.91 ms at 48; at 40 registers and six
+// CTAs, 0.93 ms).  The long long form keeps four, which it needs to avoid spills.
 template <int ROWS, typename RP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(RP) == 4 ? 5 : 4)
 split_pass_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_idx, const float *__restrict__ vals,
                   int n, int d, uint32_t B, RP nnz, Key key, int64_t row_offset, float *__restrict__ SX,
                   uint32_t bsplit, int rows_per_cta, uint2 *__restrict__ records, RP *__restrict__ counts,
@@ -322,7 +328,20 @@ size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas) {
     return align256(static_cast<size_t>(nnz) * sizeof(uint2)) + align256(static_cast<size_t>(ctas) * sizeof(long long));
 }
 
-int sketch_deferred_ctas(int ctas) { return ctas > 0 ? ctas : sketch_default_ctas(); }
+// CTAs of both passes: `ctas` when given, else one per sweep of the CTA's warps (kWarps
+// chunks of H rows; at least the one-pass scatter's grid).  Regions are whole sweeps
+// because a CTA lasts as long as its busiest warp, and many small CTAs leave no partial
+// last wave (760 are resident at once): at the 2^26-row ladder shape the pair takes
+// 0.916 ms with 1216 CTAs (1.6 waves), 0.898 ms with 10486 CTAs of 25 chunks (one warp
+// with four, the others three), 0.842 ms with 32768 CTAs of one sweep and 0.840 ms with
+// 16384 of two; at a quarter of its rows, 0.257 ms with 2048 CTAs of four sweeps and
+// 0.246 ms with 8192 of one.
+int sketch_deferred_ctas(int ctas, int64_t n, int64_t nnz, int rows) {
+    if (ctas > 0) return ctas;
+    const int64_t sweep = static_cast<int64_t>(kWarps) * staged_rows(static_cast<int>(n), nnz, rows);
+    const int64_t g = std::max<int64_t>(sketch_default_ctas(), (n + sweep - 1) / sweep);
+    return static_cast<int>(std::min<int64_t>(g, 1 << 26));
+}
 
 namespace {
 
@@ -332,10 +351,13 @@ cudaError_t sketch_deferred(const RP *row_ptr, const int *col_idx, const float *
                             int rows, const EventPair *ev, cudaStream_t stream, bool clear) {
     cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
     if (e != cudaSuccess || n == 0) return e;
-    const int G = sketch_deferred_ctas(ctas);
+    const int G = sketch_deferred_ctas(ctas, n, nnz, rows);
     const int H = staged_rows(n, nnz, rows);
+    // whole sweeps of the CTA's warps (kWarps chunks of H rows each): a CTA lasts as long
+    // as its busiest warp
     const int per = (n + G - 1) / G;
-    const int rows_per_cta = (per + H - 1) / H * H;
+    const int sweep = kWarps * H;
+    const int rows_per_cta = static_cast<int>((static_cast<int64_t>(per) + sweep - 1) / sweep * sweep);
     const int used = (n + rows_per_cta - 1) / rows_per_cta;
     uint2 *records = static_cast<uint2 *>(scratch);
     RP *counts = reinterpret_cast<RP *>(static_cast<char *>(scratch) + align256(static_cast<size_t>(nnz) * sizeof(uint2)));
