@@ -48,8 +48,28 @@ def shard_csr_cols(row_ptr: np.ndarray, col_idx: np.ndarray, vals: np.ndarray, s
     return rp, (col_idx[keep] - start).astype(col_idx.dtype), vals[keep]
 
 
-def sum_outputs(Y: torch.Tensor, group=None) -> torch.Tensor:
-    """In-place sum of the per-rank m x d outputs (row shards)."""
+def check_same_shape(t: torch.Tensor, group=None) -> None:
+    """Raise ValueError on every rank of `group` unless all ranks hold a tensor of t's shape
+    (at most four dimensions).  A collective over tensors of different sizes can hand some
+    rank a silently wrong result (gloo: the rank with the shorter tensor), so the sharded
+    calls check first, with one all-gather of four integers."""
+    if t.dim() > 4:
+        raise ValueError("check_same_shape: at most four dimensions")
+    mine = torch.tensor(list(t.shape) + [-1] * (4 - t.dim()), dtype=torch.int64)
+    shapes = [torch.empty_like(mine) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(shapes, mine, group=group)
+    if any(not torch.equal(sh, mine) for sh in shapes):
+        raise ValueError("ranks hold outputs of different shapes: " + ", ".join(
+            str(tuple(int(x) for x in sh if x >= 0)) for sh in shapes))
+
+
+def sum_outputs(Y: torch.Tensor, group=None, check: bool = True) -> torch.Tensor:
+    """In-place sum of the per-rank m x d outputs (row shards).  With `check` the ranks
+    first agree that their outputs have the same shape (check_same_shape).  A rank that
+    has died or never joins makes the collective raise on the others (the connection
+    closes, or the process group's timeout passes)."""
+    if check:
+        check_same_shape(Y, group)
     dist.all_reduce(Y, op=dist.ReduceOp.SUM, group=group)
     return Y
 
@@ -92,8 +112,10 @@ def merge_anchor_records(records: list[np.ndarray]) -> tuple[np.ndarray, np.ndar
 
 
 def gather_anchor_records(rec: np.ndarray, group=None) -> list[np.ndarray]:
-    """All ranks' records (every rank receives all, so any rank can act as coordinator)."""
+    """All ranks' records (every rank receives all, so any rank can act as coordinator).
+    The ranks first agree that their record arrays have the same shape (check_same_shape)."""
     t = torch.from_numpy(np.ascontiguousarray(rec, np.float64))
+    check_same_shape(t, group)
     out = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
     dist.all_gather(out, t, group=group)
     return [o.numpy() for o in out]

@@ -2,7 +2,7 @@
 all-reduce equal the whole transform, and column shards merged by a coordinator give
 the whole input's NMF anchors (the distributed remark of Section 4).  The per-rank
 compute is the oracle's; what is tested is the sharding, the offsets, the collective
-and the merge."""
+and the merge, and that a dead, absent or mismatched rank surfaces as an error."""
 import os
 import socket
 
@@ -74,3 +74,52 @@ def test_shard_helpers():
     ties = [np.array([[5.0, 7.0, -1.0, 9.0]]), np.array([[5.0, 2.0, -1.0, 3.0]])]
     imax, imin = cgd.merge_anchor_records(ties)
     assert imax.tolist() == [2] and imin.tolist() == [3]
+
+
+def _fault_worker(rank, world, port, out_dir, mode):
+    """One rank of a two-rank group with a short timeout; rank 1 misbehaves per `mode`,
+    rank 0 (and for "shape" both) records what the collective did."""
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=3))
+    outcome = "ok"
+    t0 = time.monotonic()
+    if mode == "dead" and rank == 1:
+        os._exit(0)  # dies before the collective, with nothing in flight
+    if mode == "absent" and rank == 1:
+        time.sleep(8.0)  # alive but never joins; leaves after the others gave up
+        os._exit(0)
+    try:
+        Y = torch.ones(4, 3 if (mode != "shape" or rank == 0) else 2, dtype=torch.float64)
+        cgd.sum_outputs(Y)
+    except ValueError as e:
+        outcome = "ValueError: " + str(e)
+    except RuntimeError as e:
+        outcome = "RuntimeError: " + str(e)[:200]
+    with open(os.path.join(out_dir, f"fault{rank}.txt"), "w") as f:
+        f.write(f"{time.monotonic() - t0:.2f}\n{outcome}\n")
+    os._exit(0)
+
+
+@pytest.mark.parametrize("mode", ["dead", "absent", "shape"])
+def test_rank_faults_surface_as_errors(tmp_path, mode):
+    """Failure detection of the combine step, on the host: a rank that dies before the
+    all-reduce, a rank that never joins it, and ranks whose outputs differ in shape.  The
+    others raise (connection closed, the process group's 3 s timeout, or the shape check
+    on every rank) instead of hanging or returning a wrong sum."""
+    import time
+    t0 = time.monotonic()
+    mp.start_processes(_fault_worker, args=(2, _free_port(), str(tmp_path), mode), nprocs=2,
+                       start_method="spawn", join=True)
+    assert time.monotonic() - t0 < 60
+    lines = (tmp_path / "fault0.txt").read_text().split("\n")
+    assert float(lines[0]) < 30
+    if mode == "shape":
+        for rank in range(2):
+            out = (tmp_path / f"fault{rank}.txt").read_text()
+            assert "ValueError: ranks hold outputs of different shapes" in out
+    else:
+        assert lines[1].startswith("RuntimeError"), lines[1]
+        assert not (tmp_path / "fault1.txt").exists()
