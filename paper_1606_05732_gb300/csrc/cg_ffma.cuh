@@ -45,7 +45,11 @@ __device__ __forceinline__ float load1(const float *p) {
 // cp.async into the second buffer while slab s's G tile is drawn and multiplied;
 // otherwise it is loaded synchronously (with COHERENT through L2, for SX written
 // earlier in the same launch).
-template <int TN, bool COHERENT>
+// UNROLLED: when one or two k-groups cover the block (256 or 128 thread tiles), the kk
+// loop runs with constant bounds and fully unrolled (shared-memory offsets become
+// immediates; the FP32 contraction at m = d = 128 went from 0.276 to 0.252 ms); off in
+// the batched kernel, whose 64-register budget it would exceed.
+template <int TN, bool COHERENT, bool UNROLLED = true>
 __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, int d, int64_t B, Key key,
                                            int64_t s_begin, int64_t s_end, int m0, int n0, bool vec_x,
                                            float *__restrict__ out, float *raw) {
@@ -125,26 +129,34 @@ __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, 
             }
         }
         __syncthreads();
-        if (active) {
-            for (int kk = grp; kk < kFfmaKT; kk += kg) {
-                const float4 a = *reinterpret_cast<const float4 *>(&sG[kk][4 * ti]);
-                float bv[TN];
+        // acc += G[4 ti .. 4 ti + 4, kk] x SX[kk, TN tj .. TN tj + TN)
+        auto step = [&](int kk) {
+            const float4 a = *reinterpret_cast<const float4 *>(&sG[kk][4 * ti]);
+            float bv[TN];
 #pragma unroll
-                for (int j4 = 0; j4 < TN / 4; ++j4) {
-                    const float4 x = *reinterpret_cast<const float4 *>(&sX[kk][TN * tj + 4 * j4]);
-                    bv[4 * j4 + 0] = x.x;
-                    bv[4 * j4 + 1] = x.y;
-                    bv[4 * j4 + 2] = x.z;
-                    bv[4 * j4 + 3] = x.w;
-                }
-#pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    acc[0][j] = fmaf(a.x, bv[j], acc[0][j]);
-                    acc[1][j] = fmaf(a.y, bv[j], acc[1][j]);
-                    acc[2][j] = fmaf(a.z, bv[j], acc[2][j]);
-                    acc[3][j] = fmaf(a.w, bv[j], acc[3][j]);
-                }
+            for (int j4 = 0; j4 < TN / 4; ++j4) {
+                const float4 x = *reinterpret_cast<const float4 *>(&sX[kk][TN * tj + 4 * j4]);
+                bv[4 * j4 + 0] = x.x;
+                bv[4 * j4 + 1] = x.y;
+                bv[4 * j4 + 2] = x.z;
+                bv[4 * j4 + 3] = x.w;
             }
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                acc[0][j] = fmaf(a.x, bv[j], acc[0][j]);
+                acc[1][j] = fmaf(a.y, bv[j], acc[1][j]);
+                acc[2][j] = fmaf(a.z, bv[j], acc[2][j]);
+                acc[3][j] = fmaf(a.w, bv[j], acc[3][j]);
+            }
+        };
+        if (UNROLLED && kg == 1) {  // every thread owns a tile and all kFfmaKT k-indices
+#pragma unroll
+            for (int kk = 0; kk < kFfmaKT; ++kk) step(kk);
+        } else if (UNROLLED && kg == 2) {  // two k-groups: k-indices grp, grp + 2, ...
+#pragma unroll
+            for (int i = 0; i < kFfmaKT / 2; ++i) step(grp + 2 * i);
+        } else if (active) {
+            for (int kk = grp; kk < kFfmaKT; kk += kg) step(kk);
         }
         __syncthreads();
     }
