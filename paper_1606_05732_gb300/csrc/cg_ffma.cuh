@@ -149,14 +149,18 @@ __device__ __forceinline__ void ffma_block(const float *__restrict__ SX, int m, 
                 acc[3][j] = fmaf(a.w, bv[j], acc[3][j]);
             }
         };
-        if (UNROLLED && kg == 1) {  // every thread owns a tile and all kFfmaKT k-indices
+        // Threads past the last k-group (grp >= kg: the block has fewer than 256 tiles and
+        // 256 is not a multiple of their count) own no k-index and take no step.
+        if (active) {
+            if (UNROLLED && kg == 1) {  // one k-group: every k-index of the slab
 #pragma unroll
-            for (int kk = 0; kk < kFfmaKT; ++kk) step(kk);
-        } else if (UNROLLED && kg == 2) {  // two k-groups: k-indices grp, grp + 2, ...
+                for (int kk = 0; kk < kFfmaKT; ++kk) step(kk);
+            } else if (UNROLLED && kg == 2) {  // two k-groups: k-indices grp, grp + 2, ...
 #pragma unroll
-            for (int i = 0; i < kFfmaKT / 2; ++i) step(grp + 2 * i);
-        } else if (active) {
-            for (int kk = grp; kk < kFfmaKT; kk += kg) step(kk);
+                for (int i = 0; i < kFfmaKT / 2; ++i) step(grp + 2 * i);
+            } else {
+                for (int kk = grp; kk < kFfmaKT; kk += kg) step(kk);
+            }
         }
         __syncthreads();
     }

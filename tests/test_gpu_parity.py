@@ -395,6 +395,22 @@ def test_contract_alone_and_deterministic():
     assert rel(Y1, oracle.contract(seed, m, SXn)) < FP32_TOL
 
 
+@pytest.mark.parametrize("m,d", [(96, 96), (40, 64), (130, 200), (33, 130), (8, 16), (64, 128)])
+def test_contract_blocks_with_idle_threads(m, d):
+    """Output blocks of fewer than 256 thread tiles, where 256 is not a multiple of their
+    count (96 x 96: a block of 96 tiles leaves threads past the second k-group; 40 x 64:
+    160 tiles), besides full blocks: the FFMA contraction against the oracle, twice."""
+    B, seed = 4096, 11
+    SXn = np.random.default_rng(m * 1000 + d).standard_normal((B, d)).astype(np.float32)
+    plan = cg().CountGauss(10, d, m, B, seed)
+    SX = torch.from_numpy(SXn).cuda()
+    Y1 = plan.contract(SX).cpu().numpy()
+    Y2 = plan.contract(SX).cpu().numpy()
+    plan.check()
+    np.testing.assert_array_equal(Y1, Y2)
+    assert rel(Y1, oracle.contract(seed, m, SXn)) < FP32_TOL
+
+
 def test_empty_inputs():
     n, d, m, B = 200, 8, 8, 32
     X = synth.csr_bernoulli(n, d, 0.0, seed=1)
