@@ -3,7 +3,8 @@
 //
 // One fp32 reduction per nonzero runs at the L2's atomic rate only while the reduced
 // array stays in L2; past that (on GB300 from about 100 MB on) most reductions miss and
-// the rate falls several-fold.  So SX is split at bucket bsplit = B/2:
+// the rate falls several-fold.  So SX is split at bucket bsplit (B/2, or more so that the
+// lower part fills about 0.55 of the L2; deferred_split):
 //   pass 1  streams the CSR once, hashes every row once, reduces the nonzeros of rows
 //           with h < bsplit into SX at once, and writes those of the other rows as
 //           8-byte records (h d + j, sigma x) into its CTA's region of a records buffer
@@ -12,9 +13,10 @@
 //           hands out slots, so records are written compactly and coalesced);
 //   pass 2  streams each region's records and reduces them into the upper part of SX,
 //           which is then the one in L2.
-// Each half of SX is half the size, and the extra traffic is the records, 16 bytes per
-// deferred nonzero (written once, read once, with an evict-first L2 policy).  Sums are
-// fp32 in an order that depends on timing, as with the atomic scatter.  Both passes are
+// Each part of SX stays within the L2 (for an SX up to about 1.1 times its size), and the
+// extra traffic is the records, 16 bytes per deferred nonzero (written once, read once,
+// with an evict-first L2 policy).  Sums are fp32 in an order that depends on timing, as
+// with the atomic scatter.  Both passes are
 // templated on the type of the row offsets: int, or long long for matrices of 2^31
 // nonzeros or more (warp chunks rebased to their first nonzero, 64-bit record indices
 // and per-CTA counts).
@@ -337,6 +339,22 @@ int staged_rows(int n, int64_t nnz, int forced) {
     return 256;
 }
 
+// The bucket below which pass 1 reduces at once: for an SX past 60 % of the L2 (where the
+// automatic choice takes this scatter), the largest that keeps that part of SX at 0.55 of
+// the L2 (about 73 MB on GB300), and at least B/2 so that the part the records fill is no
+// larger; for a smaller SX (the scatter forced) B/2.  At the 2^18 x 128 ladder shape (134
+// MB of SX) 0.54 B took the step from 1.070 to 1.044 ms; at 2^18 x 96 (101 MB) 0.65 B from
+// 0.472 to 0.459 ms -- past that point the lower part's reductions leave the L2, short of
+// it the records cost more instructions in pass 1 than the direct reductions they replace.
+uint32_t deferred_split(uint32_t B, int d) {
+    const uint32_t half = B / 2;
+    const int l2 = l2_bytes();
+    const double sx = static_cast<double>(B) * d * sizeof(float);
+    if (l2 <= 0 || d <= 0 || sx <= 0.6 * l2) return half;
+    const uint64_t fit = static_cast<uint64_t>(0.55 * l2) / (static_cast<uint64_t>(d) * sizeof(float));
+    return static_cast<uint32_t>(std::min<uint64_t>(B, std::max<uint64_t>(half, fit)));
+}
+
 }  // namespace
 
 bool deferred_supported(int64_t B, int d) { return static_cast<uint64_t>(B) * static_cast<uint64_t>(d) < (1ull << 32); }
@@ -378,7 +396,7 @@ cudaError_t sketch_deferred(const RP *row_ptr, const int *col_idx, const float *
     const int used = (n + rows_per_cta - 1) / rows_per_cta;
     uint2 *records = static_cast<uint2 *>(scratch);
     RP *counts = reinterpret_cast<RP *>(static_cast<char *>(scratch) + align256(static_cast<size_t>(nnz) * sizeof(uint2)));
-    const uint32_t bsplit = B / 2;
+    const uint32_t bsplit = deferred_split(B, d);
     record(ev, true, stream);
     switch (H) {
         case 256:

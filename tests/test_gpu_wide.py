@@ -168,7 +168,7 @@ def test_deferred_past_2_pow_31_nonzeros_matches_row_blocks_and_oracle():
     18 GB of CSR) into an SX of 2^18 x 128 (128 MB, past the L2): the automatic choice is
     the deferred scatter with int64 offsets (its workspace holds 8 bytes per nonzero).  Y
     equals the sum of the 32-bit path over two row blocks; SX at 64 sampled buckets, half
-    of them at or above B/2 (the rows reduced by the replay pass), equals the definition
+    of them in the top quarter (rows the replay pass reduces), equals the definition
     (sum of sigma(i) X[i, :] over the rows with h(i) = b, h and sigma from the oracle) in
     FP64."""
     from paper_1606_05732_gb300 import _lib
@@ -194,7 +194,7 @@ def test_deferred_past_2_pow_31_nonzeros_matches_row_blocks_and_oracle():
     plan.check()
     rng = np.random.default_rng(seed)
     sample = np.concatenate([rng.choice(B // 2, 32, replace=False),
-                             B // 2 + rng.choice(B // 2, 32, replace=False)]).astype(np.int64)
+                             3 * B // 4 + rng.choice(B // 4, 32, replace=False)]).astype(np.int64)
     h, sg = oracle.hash_sign(seed, B, 0, n)
     rows = np.nonzero(np.isin(h, sample))[0]
     rows_d = torch.from_numpy(rows).cuda()
