@@ -90,7 +90,13 @@ typedef enum cg_option {
     CG_OPT_PRECISION = 1,     /* cg_precision of the Gaussian contraction (default FP32) */
     CG_OPT_DETERMINISTIC = 2, /* 0: fp32 atomic scatter (default); 1: exact int64 fixed-point
                                  sums of the scatter, rounded once to fp32: independent of
-                                 the order of the reductions, so bit-reproducible run to run */
+                                 the order of the reductions, so bit-reproducible run to run.
+                                 The sums live in one int64 array of B x d in the workspace, or,
+                                 once that array is larger than 60 % of the L2 (or with
+                                 CG_OPT_SCATTER = 4), in shared memory one slice of buckets at
+                                 a time (workspace about 14 bytes per nonzero; needs
+                                 d <= 16384 and at most 2048 slices); CG_OPT_SCATTER = 1 keeps
+                                 the array.  Both forms give the same bits. */
     CG_OPT_ROW_OFFSET = 3,    /* global index of local row 0 (default 0) */
     CG_OPT_KSPLIT = 4,        /* CTAs along B in the contraction; 0 = automatic */
     CG_OPT_SKETCH_CTAS = 5,   /* CTAs of the scatter kernel; 0 = automatic */

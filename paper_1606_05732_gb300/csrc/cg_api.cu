@@ -235,6 +235,20 @@ bool sx_past_l2(const cg_plan &p) {
     return l2 > 0 && sx > 0.6 * l2;
 }
 
+// Whether the deterministic mode bins the nonzeros by bucket slice and sums each slice in
+// int64 fixed point in shared memory: when its int64 accumulator (8 B d bytes) would not
+// fit the L2 (60 % of it), where the fixed-point reductions into global memory slow down
+// several-fold; the sums are the same integers, so the result is bit-identical.
+// CG_OPT_SCATTER = 4 asks for the slices, 1 for the global accumulator.
+bool use_binned_fixed(const cg_plan &p) {
+    if (!p.deterministic || !binned_supported(p.n, p.d, p.B, true)) return false;
+    if (p.scatter == 4) return true;
+    if (p.scatter == 1) return false;
+    const double acc = 8.0 * static_cast<double>(p.B) * p.d;
+    const int l2 = l2_bytes();
+    return l2 > 0 && acc > 0.6 * l2;
+}
+
 // Whether a CSR scatter through plan p bins the nonzeros by bucket slice and sums each
 // slice in shared memory: on request (CG_OPT_SCATTER = 4) only; on GB300 at the largest
 // workload it measures slightly slower than the deferred scatter (0.98 against 0.93 ms).
@@ -255,7 +269,9 @@ bool use_deferred(const cg_plan &p, int64_t nnz) {
 
 // Scratch bytes of the CSR scatter through plan p (region C).
 size_t scatter_scratch(const cg_plan &p, int64_t nnz, PartLayout *part) {
-    if (p.deterministic) return sketch_fixed_scratch_bytes(p.B, p.d);
+    if (p.deterministic)
+        return use_binned_fixed(p) ? sketch_binned_scratch_bytes(p.n, p.d, p.B, nnz, static_cast<int>(p.sketch_ctas), true)
+                                   : sketch_fixed_scratch_bytes(p.B, p.d);
     if (use_partition(p)) {
         *part = partition_layout(p, nnz);
         return part->bytes;
@@ -406,6 +422,12 @@ cg_status run_contract(cg_plan *p, const float *SX, float *Y, void *ws, const La
 cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_idx, const float *vals,
                          int64_t nnz, float *SX, void *ws, const Layout &L, cudaStream_t st, bool clear = true,
                          bool host_mapped = false) {
+    if (p->deterministic && use_binned_fixed(*p))
+        return from_cuda(launch_sketch_csr_binned(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
+                                                  static_cast<uint32_t>(p->B), static_cast<int>(nnz),
+                                                  make_key(p->seed), p->row_offset, SX, status_word(ws),
+                                                  region(ws, L.c_off), static_cast<int>(p->sketch_ctas),
+                                                  timing_pair(p, CG_KERNEL_SKETCH), st, true, !host_mapped, true));
     if (p->deterministic)
         return from_cuda(launch_sketch_csr_fixed(row_ptr, col_idx, vals, static_cast<int>(p->n), p->d,
                                                  static_cast<uint32_t>(p->B), static_cast<int>(nnz), make_key(p->seed),

@@ -128,6 +128,14 @@ int sketch_default_ctas();
 cudaError_t launch_sketch_csr_rows_chunk(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                          uint32_t B, int klo, int khi, Key key, int64_t row_offset, float *SX,
                                          int *status, int ctas, int rows, cudaStream_t stream);
+// max |x| over the finite values into maxbits[0] (bit pattern of a non-negative float,
+// atomicMax) and a non-finite flag into maxbits[1]; the caller zeroes both first.
+cudaError_t launch_absmax(const float *vals, int nnz, int *maxbits, cudaStream_t stream);
+// Adds every non-finite entry's sigma x to its cell of SX when maxbits[1] is set (the rule
+// of the fixed-point sums for NaN and infinities).
+cudaError_t launch_add_nonfinite(const int *row_ptr, const int *col_idx, const float *vals, int n, int d, uint32_t B,
+                                 int nnz, Key key, int64_t row_offset, const int *maxbits, float *SX,
+                                 cudaStream_t stream);
 // Deterministic scatter: exact int64 fixed-point sums (scratch of sketch_fixed_scratch_bytes).
 size_t sketch_fixed_scratch_bytes(int64_t B, int d);
 cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
@@ -159,12 +167,15 @@ cudaError_t launch_sketch_csr_deferred_i64(const long long *row_ptr, const int *
 // ---- binned scatter (cg_sketch_bin.cu) -----------------------------------------
 // Nonzeros binned by bucket range (slices of SX that fit in shared memory), each slice
 // summed in shared memory and written once (for an SX larger than the L2 holds).
-bool binned_supported(int64_t n, int d, int64_t B);
-size_t sketch_binned_scratch_bytes(int64_t n, int d, int64_t B, int64_t nnz, int ctas);
+// With `fixed` the slices hold int64 fixed-point sums (half the buckets per slice): the
+// deterministic mode's exact, order-independent sums, bit-identical to those of
+// launch_sketch_csr_fixed.
+bool binned_supported(int64_t n, int d, int64_t B, bool fixed = false);
+size_t sketch_binned_scratch_bytes(int64_t n, int d, int64_t B, int64_t nnz, int ctas, bool fixed = false);
 cudaError_t launch_sketch_csr_binned(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                      void *scratch, int ctas, const EventPair *ev, cudaStream_t stream,
-                                     bool clear = true, bool prefetch = true);
+                                     bool clear = true, bool prefetch = true, bool fixed = false);
 
 // Bytes of the L2 of the current device (cached per device; 0 without a device).
 int l2_bytes();

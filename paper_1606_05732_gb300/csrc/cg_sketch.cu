@@ -360,6 +360,23 @@ cudaError_t launch_sketch_csr_rows_chunk(const int *row_ptr, const int *col_idx,
     return cudaGetLastError();
 }
 
+cudaError_t launch_absmax(const float *vals, int nnz, int *maxbits, cudaStream_t stream) {
+    if (nnz <= 0) return cudaSuccess;
+    const int sms = num_sms() > 0 ? num_sms() : 148;
+    absmax_kernel<<<sms * (2048 / kThreads), kThreads, 0, stream>>>(vals, nnz, maxbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_nonfinite(const int *row_ptr, const int *col_idx, const float *vals, int n, int d, uint32_t B,
+                                 int nnz, Key key, int64_t row_offset, const int *maxbits, float *SX,
+                                 cudaStream_t stream) {
+    if (nnz <= 0 || n <= 0) return cudaSuccess;
+    const int sms = num_sms() > 0 ? num_sms() : 148;
+    add_nonfinite_kernel<<<sms * 2, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset,
+                                                           maxbits, SX);
+    return cudaGetLastError();
+}
+
 size_t sketch_fixed_scratch_bytes(int64_t B, int d) {
     return 256 + static_cast<size_t>(B) * d * sizeof(unsigned long long);
 }

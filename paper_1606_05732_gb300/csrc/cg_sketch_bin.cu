@@ -323,12 +323,18 @@ __global__ void __launch_bounds__(kBinThreads, RPL <= 8 ? 2 : 1) bin_pass_kernel
 
 // Pass 2: CTA s sums slice s (buckets [s SB, min((s+1) SB, B))) of SX in shared memory
 // from its record stream and writes it once (adding to SX when `accumulate`); the last CTA
-// to arrive adds the overflow records.
+// to arrive adds the overflow records.  With FIXED the slice holds int64 fixed-point sums
+// (to_fixed(x, F), F from maxbits and nnz as in the deterministic scatter), each CTA adds
+// the overflow records of its own slice before the one rounding to fp32 -- exact and
+// order-independent, so the result is bit-identical to the fixed-point scatter's.
+template <bool FIXED>
 __global__ void __launch_bounds__(kReduceThreads)
 bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ rvals, int *__restrict__ cursor,
                   int P, int scap, int sb_log2, int d, uint32_t B, float *__restrict__ SX, int accumulate, int ocap,
-                  const uint2 *__restrict__ orec) {
-    extern __shared__ __align__(16) float slice[];
+                  const uint2 *__restrict__ orec, const int *__restrict__ maxbits, int nnz) {
+    extern __shared__ __align__(16) unsigned char slice_raw[];
+    float *slice = reinterpret_cast<float *>(slice_raw);
+    unsigned long long *slice64 = reinterpret_cast<unsigned long long *>(slice_raw);
     __shared__ int s_last;
     const int s = blockIdx.x, t = threadIdx.x;
     const uint32_t b0 = static_cast<uint32_t>(s) << sb_log2;
@@ -336,7 +342,8 @@ bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ 
     const uint32_t nf = nb * static_cast<uint32_t>(d);
     float *dst = SX + static_cast<size_t>(b0) * d;
     const bool vec = (nf & 3u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
-    pdl_wait();  // pass 1 wrote the streams
+    pdl_wait();  // pass 1 wrote the streams (and the max-|x| pass maxbits)
+    const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
     const int cnt = min(__ldg(cursor + s), scap);
     const long long at = static_cast<long long>(s) * scap;  // 16-byte aligned: scap is a multiple of 8
     const uint16_t *keys = rkeys + at;
@@ -345,7 +352,9 @@ bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ 
         prefetch_l2(keys, keys + cnt);
         prefetch_l2(vs, vs + cnt);
     }
-    if (vec) {
+    if (FIXED) {
+        for (uint32_t i = t; i < nf; i += kReduceThreads) slice64[i] = 0ull;
+    } else if (vec) {
         for (uint32_t i = t; i < (nf >> 2); i += kReduceThreads)
             reinterpret_cast<float4 *>(slice)[i] =
                 accumulate ? reinterpret_cast<const float4 *>(dst)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -353,6 +362,12 @@ bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ 
         for (uint32_t i = t; i < nf; i += kReduceThreads) slice[i] = accumulate ? dst[i] : 0.0f;
     }
     __syncthreads();
+    auto add = [&](uint32_t k, float v) {
+        if (FIXED)
+            atomicAdd(slice64 + k, to_fixed(v, F));
+        else
+            atomicAdd(slice + k, v);
+    };
     const uint64_t pol = l2_evict_first_policy();
     const int n8 = cnt >> 3;
     constexpr int kIn = 2;  // groups of eight records in flight per thread
@@ -382,12 +397,25 @@ bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ 
             const float vv[8] = {v0[u].x, v0[u].y, v0[u].z, v0[u].w, v1[u].x, v1[u].y, v1[u].z, v1[u].w};
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-                if (kk[e] < nf) atomicAdd(slice + kk[e], vv[e]);
+                if (kk[e] < nf) add(kk[e], vv[e]);
         }
     }
     for (int i = (n8 << 3) + t; i < cnt; i += kReduceThreads) {
         const uint32_t k = keys[i];
-        if (k < nf) atomicAdd(slice + k, vs[i]);
+        if (k < nf) add(k, vs[i]);
+    }
+    if (FIXED) {
+        // the overflow records of this slice (pass 1 finished: their count is final)
+        const int no = min(__ldg(cursor + P), ocap);
+        const uint32_t c0 = b0 * static_cast<uint32_t>(d);
+        for (int i = t; i < no; i += kReduceThreads) {
+            const uint2 r = __ldg(orec + i);
+            if (r.x >= c0 && r.x - c0 < nf) add(r.x - c0, __uint_as_float(r.y));
+        }
+        __syncthreads();
+        for (uint32_t i = t; i < nf; i += kReduceThreads)
+            dst[i] = ldexpf(__ll2float_rn(static_cast<long long>(slice64[i])), -F);
+        return;
     }
     __syncthreads();
     if (vec) {
@@ -422,21 +450,23 @@ int rows_per_lane(int64_t n, int64_t nnz, int T) {
     return r;
 }
 
-// log2 of the buckets per slice: the largest power of two SB with SB d <= kSliceFloats.
-int slice_log2(int d) {
+// log2 of the buckets per slice: the largest power of two SB whose SB d cells fit the
+// 128 KB slice (kSliceFloats fp32 cells, or half as many int64 cells with `fixed`).
+int slice_log2(int d, bool fixed = false) {
+    const int64_t cells = fixed ? kSliceFloats / 2 : kSliceFloats;
     int l = 0;
-    while ((2LL << l) * d <= kSliceFloats) ++l;
+    while ((2LL << l) * d <= cells) ++l;
     return l;
 }
 
 struct BinPlan {
     int sb_log2 = 0, P = 0, G = 0, RPL = 1, rows_per_cta = 0, T = kStageRecords, scap = 0;
-    size_t keys_off = 0, vals_off = 0, cursor_off = 0, orec_off = 0, bytes = 0;
+    size_t keys_off = 0, vals_off = 0, cursor_off = 0, orec_off = 0, maxbits_off = 0, bytes = 0;
 };
 
-BinPlan bin_plan(int64_t n, int d, int64_t B, int64_t nnz, int ctas) {
+BinPlan bin_plan(int64_t n, int d, int64_t B, int64_t nnz, int ctas, bool fixed = false) {
     BinPlan L;
-    L.sb_log2 = slice_log2(d);
+    L.sb_log2 = slice_log2(d, fixed);
     L.P = static_cast<int>((B + (1LL << L.sb_log2) - 1) >> L.sb_log2);
     const int sms = num_sms() > 0 ? num_sms() : 148;
     const int G = ctas > 0 ? ctas : 2 * sms;
@@ -460,6 +490,7 @@ BinPlan bin_plan(int64_t n, int d, int64_t B, int64_t nnz, int ctas) {
     L.vals_off = take(records * sizeof(float));
     L.cursor_off = take((static_cast<size_t>(L.P) + 2) * sizeof(int));
     L.orec_off = take(static_cast<size_t>(std::max<int64_t>(nnz, 1)) * sizeof(uint2));
+    L.maxbits_off = take(fixed ? 2 * sizeof(int) : 0);
     L.bytes = off;
     return L;
 }
@@ -481,22 +512,22 @@ cudaError_t launch_bin_pass(const BinPlan &L, const BinArgs &a, cudaStream_t str
 
 }  // namespace
 
-bool binned_supported(int64_t n, int d, int64_t B) {
-    if (d > kSliceFloats || n <= 0) return false;
-    const int l = slice_log2(d);
+bool binned_supported(int64_t n, int d, int64_t B, bool fixed) {
+    if (d > (fixed ? kSliceFloats / 2 : kSliceFloats) || n <= 0) return false;
+    const int l = slice_log2(d, fixed);
     const int64_t P = (B + (1LL << l) - 1) >> l;
     return P <= kMaxSlices && static_cast<uint64_t>(P << l) * static_cast<uint64_t>(d) < (1ull << 32);
 }
 
-size_t sketch_binned_scratch_bytes(int64_t n, int d, int64_t B, int64_t nnz, int ctas) {
-    return bin_plan(n, d, B, nnz, ctas).bytes;
+size_t sketch_binned_scratch_bytes(int64_t n, int d, int64_t B, int64_t nnz, int ctas, bool fixed) {
+    return bin_plan(n, d, B, nnz, ctas, fixed).bytes;
 }
 
 cudaError_t launch_sketch_csr_binned(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                      uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                      void *scratch, int ctas, const EventPair *ev, cudaStream_t stream, bool clear,
-                                     bool prefetch) {
-    const BinPlan L = bin_plan(n, d, B, nnz, ctas);
+                                     bool prefetch, bool fixed) {
+    const BinPlan L = bin_plan(n, d, B, nnz, ctas, fixed);
     char *base = static_cast<char *>(scratch);
     BinArgs a;
     a.row_ptr = row_ptr;
@@ -520,9 +551,12 @@ cudaError_t launch_sketch_csr_binned(const int *row_ptr, const int *col_idx, con
     a.orec = reinterpret_cast<uint2 *>(base + L.orec_off);
     a.ocap = std::max(nnz, 1);
     a.status = status;
+    int *maxbits = fixed ? reinterpret_cast<int *>(base + L.maxbits_off) : nullptr;
     cudaError_t e = cudaMemsetAsync(a.cursor, 0, (static_cast<size_t>(L.P) + 2) * sizeof(int), stream);
+    if (e == cudaSuccess && fixed) e = cudaMemsetAsync(maxbits, 0, 2 * sizeof(int), stream);
     if (e != cudaSuccess) return e;
     record(ev, true, stream);
+    if (fixed && (e = launch_absmax(vals, nnz, maxbits, stream)) != cudaSuccess) return e;
     switch (L.RPL) {
         case 1: e = launch_bin_pass<1>(L, a, stream); break;
         case 2: e = launch_bin_pass<2>(L, a, stream); break;
@@ -531,14 +565,18 @@ cudaError_t launch_sketch_csr_binned(const int *row_ptr, const int *col_idx, con
         default: e = launch_bin_pass<16>(L, a, stream); break;
     }
     if (e != cudaSuccess) return e;
-    const size_t smem2 = (static_cast<size_t>(1) << L.sb_log2) * d * sizeof(float);
-    if ((e = cudaFuncSetAttribute(bin_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem2))) != cudaSuccess)
+    const size_t smem2 = (static_cast<size_t>(1) << L.sb_log2) * d * (fixed ? sizeof(unsigned long long) : sizeof(float));
+    auto reduce = fixed ? bin_reduce_kernel<true> : bin_reduce_kernel<false>;
+    if ((e = cudaFuncSetAttribute(reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2))) !=
+        cudaSuccess)
         return e;
-    e = launch_after_previous(bin_reduce_kernel, dim3(L.P), dim3(kReduceThreads), smem2, stream,
+    e = launch_after_previous(reduce, dim3(L.P), dim3(kReduceThreads), smem2, stream,
                               static_cast<const uint16_t *>(a.rkeys), static_cast<const float *>(a.rvals), a.cursor,
                               L.P, L.scap, L.sb_log2, d, B, SX, clear ? 0 : 1, a.ocap,
-                              static_cast<const uint2 *>(a.orec));
+                              static_cast<const uint2 *>(a.orec), static_cast<const int *>(maxbits), nnz);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && fixed)
+        e = launch_add_nonfinite(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, maxbits, SX, stream);
     record(ev, false, stream);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();

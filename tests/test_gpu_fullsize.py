@@ -151,3 +151,39 @@ def test_fullsize_deterministic_mode_nmf():
     assert (np.abs(SX1.astype(np.float64) - SXo) <= bound).all()
     assert (SX1 == want).mean() > 0.99
     assert rel(Y, Yo) < FP32_TOL
+
+
+def test_fullsize_deterministic_mode_ladder():
+    """Deterministic mode at the largest workload (2^26 x 128, 85.9 M nonzeros), whose int64
+    accumulator (268 MB) is past the L2, so the automatic form sums bucket slices in shared
+    memory: bit-identical over two runs and to the global-accumulator form
+    (CG_OPT_SCATTER = 1), every SX entry within one fp32 ulp plus the fixed-point resolution
+    per term of the oracle's FP64 sum, and Y within the FP32 bar."""
+    from paper_1606_05732_gb300 import countgauss
+    X, w = synth.workload_csr("ladder_n64M_d128")
+    dev = torch.device("cuda", 0)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).to(dev)
+    ci = torch.from_numpy(X.col_idx).to(dev)
+    v = torch.from_numpy(X.vals).to(dev)
+    plan = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"], deterministic=True)
+    SX1 = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    SX2 = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    del plan
+    glob = countgauss.CountGauss(X.n, X.d, w["m"], w["B"], w["seed"], deterministic=True, scatter="atomic")
+    SXg = glob.sketch_csr(rp, ci, v).cpu().numpy()
+    glob.check()
+    del glob, rp, ci, v
+    torch.cuda.empty_cache()
+    np.testing.assert_array_equal(SX1, SX2)
+    np.testing.assert_array_equal(SX1, SXg)
+    Yo, SXo = oracle.apply_csr(w["seed"], X.n, X.d, w["m"], w["B"], X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    want = SXo.astype(np.float32)
+    L = max(1, int(X.nnz).bit_length())
+    e = int(np.frexp(np.abs(X.vals).max())[1])
+    per_term = 2.0 ** (L + e - 62)
+    rows_per_bucket = np.bincount(oracle.hash_sign(w["seed"], w["B"], 0, X.n)[0], minlength=w["B"])
+    bound = np.spacing(np.abs(want)).astype(np.float64) + (rows_per_bucket[:, None] + 1) * per_term
+    assert (np.abs(SX1.astype(np.float64) - SXo) <= bound).all()
+    assert rel(Y, Yo) < FP32_TOL

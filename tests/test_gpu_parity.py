@@ -161,7 +161,8 @@ def _nan_inf_equal(got, want):
     assert rel(got[fin], want[fin]) < 1e-6
 
 
-@pytest.mark.parametrize("mode", ["atomic", "deferred", "binned", "partition", "deterministic"])
+@pytest.mark.parametrize("mode", ["atomic", "deferred", "binned", "partition", "deterministic",
+                                  "deterministic_binned"])
 def test_nonfinite_values_propagate_as_ieee_addition(mode):
     """The rule for NaN and infinite entries of X, the same in every scatter: the SX cell
     they land in is NaN if it receives a NaN or both +Inf and -Inf, else the infinity it
@@ -186,7 +187,8 @@ def test_nonfinite_values_propagate_as_ieee_addition(mode):
     Xd[1234, 1] = -np.inf
     X = synth.csr_from_dense(Xd)
     rp, ci, v = dev_csr(X)
-    kw = {"deterministic": True} if mode == "deterministic" else {"scatter": mode}
+    kw = ({"deterministic": True} if mode == "deterministic" else
+          {"deterministic": True, "scatter": "binned"} if mode == "deterministic_binned" else {"scatter": mode})
     plan = cg().CountGauss(n, d, m, B, seed, **kw)
     SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
     Y = plan.apply_csr(rp, ci, v).cpu().numpy()
@@ -195,7 +197,7 @@ def test_nonfinite_values_propagate_as_ieee_addition(mode):
     assert np.isnan(SXo[h[i1], 3]) and np.isnan(SXo).sum() == 2 and np.isinf(SXo).sum() == 2
     _nan_inf_equal(SX, SXo)
     _nan_inf_equal(Y, Yo)
-    if mode == "deterministic":
+    if mode.startswith("deterministic"):
         np.testing.assert_array_equal(plan.sketch_csr(rp, ci, v).cpu().numpy(), SX)
 
 
@@ -342,6 +344,44 @@ def test_binned_overflow_and_long_tiles():
     SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
     plan.check()
     assert rel(SX, oracle.sketch_csr(seed, n, d, B, X.row_ptr, X.col_idx, X.vals)) < 1e-6
+
+
+@pytest.mark.parametrize("n,d,B,seed,kind", [(70001, 37, 3001, 21, "ragged6"), (4099, 64, 512, 22, "ragged64"),
+                                             (100_000, 16, 4096, 23, "ragged1"), (20000, 129, 1 << 13, 24, "bern"),
+                                             (256, 4096, 512, 25, "full"), (20000, 512, 1 << 14, 26, "heavy_row")])
+def test_deterministic_binned_slices_equal_global_accumulator(n, d, B, seed, kind):
+    """The deterministic mode's two forms -- one int64 accumulator in global memory
+    (CG_OPT_SCATTER = 1) and int64 sums per bucket slice in shared memory (= 4, automatic
+    once the accumulator outgrows the L2) -- add the same fixed-point integers and round once,
+    so they agree bit for bit, also where a slice's records spill to the overflow list (full
+    rows of 4096 entries; one row holding a quarter of the entries), and with the oracle."""
+    if kind.startswith("ragged"):
+        X = synth.csr_ragged(n, d, seed=seed, max_row=int(kind[6:]))
+    elif kind == "bern":
+        X = synth.csr_bernoulli(n, d, 0.03, seed=seed)
+    elif kind == "full":
+        X = synth.csr_bernoulli(n, d, 1.0, seed=seed)
+    else:
+        Xs = synth.csr_bernoulli(n, d, 0.01, seed=seed).to_dense()
+        Xs[777, :] = np.random.default_rng(1).standard_normal(d).astype(np.float32)
+        X = synth.csr_from_dense(Xs)
+    rp, ci, v = dev_csr(X)
+    m = 8
+    glob = cg().CountGauss(n, d, m, B, seed, deterministic=True, scatter="atomic")
+    bins = cg().CountGauss(n, d, m, B, seed, deterministic=True, scatter="binned")
+    SXg = glob.sketch_csr(rp, ci, v).cpu().numpy()
+    SXb = bins.sketch_csr(rp, ci, v).cpu().numpy()
+    SXb2 = bins.sketch_csr(rp, ci, v).cpu().numpy()
+    Yb = bins.apply_csr(rp, ci, v).cpu().numpy()
+    Yg = glob.apply_csr(rp, ci, v).cpu().numpy()
+    glob.check()
+    bins.check()
+    np.testing.assert_array_equal(SXb, SXg)
+    np.testing.assert_array_equal(SXb2, SXb)
+    np.testing.assert_array_equal(Yb, Yg)
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, return_sx=True)
+    assert rel(SXb, SXo) < 1e-6
+    assert rel(Yb, Yo) < FP32_TOL
 
 
 def test_partition_overflow_path():
