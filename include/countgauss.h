@@ -94,9 +94,9 @@ typedef enum cg_option {
                                  The sums live in one int64 array of B x d in the workspace, or,
                                  once that array is larger than 60 % of the L2 (or with
                                  CG_OPT_SCATTER = 4), in shared memory one slice of buckets at
-                                 a time (workspace about 14 bytes per nonzero; needs
-                                 d <= 16384 and at most 2048 slices); CG_OPT_SCATTER = 1 keeps
-                                 the array.  Both forms give the same bits. */
+                                 a time (the binned scatter's slices and workspace, option 4
+                                 of CG_OPT_SCATTER); CG_OPT_SCATTER = 1 keeps the array.
+                                 Both forms give the same bits. */
     CG_OPT_ROW_OFFSET = 3,    /* global index of local row 0 (default 0) */
     CG_OPT_KSPLIT = 4,        /* CTAs along B in the contraction; 0 = automatic */
     CG_OPT_SKETCH_CTAS = 5,   /* CTAs of the scatter kernel; 0 = automatic */

@@ -36,6 +36,7 @@ constexpr int kBinThreads = 512;
 constexpr int kReduceThreads = 1024;
 constexpr uint32_t kNoKey = 0xFFFFu;  // a record that adds nothing (bad column index)
 constexpr int kSliceFloats = 32768;   // shared-memory slice of SX: 128 KB at most
+constexpr uint32_t kFixedCells = 16384;  // int64 cells of one reduce CTA in the fixed-point form
 constexpr int kMaxSlices = 2048;
 constexpr int kStageRecords = 5632;   // records of a tile sorted in shared memory (two CTAs per SM)
 
@@ -323,24 +324,29 @@ __global__ void __launch_bounds__(kBinThreads, RPL <= 8 ? 2 : 1) bin_pass_kernel
 
 // Pass 2: CTA s sums slice s (buckets [s SB, min((s+1) SB, B))) of SX in shared memory
 // from its record stream and writes it once (adding to SX when `accumulate`); the last CTA
-// to arrive adds the overflow records.  With FIXED the slice holds int64 fixed-point sums
-// (to_fixed(x, F), F from maxbits and nnz as in the deterministic scatter), each CTA adds
-// the overflow records of its own slice before the one rounding to fp32 -- exact and
+// to arrive adds the overflow records.  With FIXED the cells hold int64 fixed-point sums
+// (to_fixed(x, F), F from maxbits and nnz as in the deterministic scatter), `parts` CTAs
+// share a slice (each reads the whole stream and keeps its cells), and each CTA adds the
+// overflow records of its own cells before the one rounding to fp32 -- exact and
 // order-independent, so the result is bit-identical to the fixed-point scatter's.
 template <bool FIXED>
 __global__ void __launch_bounds__(kReduceThreads)
 bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ rvals, int *__restrict__ cursor,
                   int P, int scap, int sb_log2, int d, uint32_t B, float *__restrict__ SX, int accumulate, int ocap,
-                  const uint2 *__restrict__ orec, const int *__restrict__ maxbits, int nnz) {
+                  const uint2 *__restrict__ orec, const int *__restrict__ maxbits, int nnz, int parts) {
     extern __shared__ __align__(16) unsigned char slice_raw[];
     float *slice = reinterpret_cast<float *>(slice_raw);
     unsigned long long *slice64 = reinterpret_cast<unsigned long long *>(slice_raw);
     __shared__ int s_last;
-    const int s = blockIdx.x, t = threadIdx.x;
+    // With FIXED, `parts` CTAs share slice s, CTA `part` summing its cells
+    // [part kFixedCells, (part + 1) kFixedCells) (an int64 cell takes twice the bytes).
+    const int s = blockIdx.x / parts, part = blockIdx.x % parts, t = threadIdx.x;
     const uint32_t b0 = static_cast<uint32_t>(s) << sb_log2;
     const uint32_t nb = min(1u << sb_log2, B - b0);
-    const uint32_t nf = nb * static_cast<uint32_t>(d);
-    float *dst = SX + static_cast<size_t>(b0) * d;
+    const uint32_t nf_slice = nb * static_cast<uint32_t>(d);
+    const uint32_t lo = FIXED ? static_cast<uint32_t>(part) * kFixedCells : 0u;
+    const uint32_t nf = FIXED ? (nf_slice > lo ? min(nf_slice - lo, kFixedCells) : 0u) : nf_slice;
+    float *dst = SX + static_cast<size_t>(b0) * d + lo;
     const bool vec = (nf & 3u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
     pdl_wait();  // pass 1 wrote the streams (and the max-|x| pass maxbits)
     const int F = FIXED ? fixed_point_exponent(*maxbits, nnz) : 0;
@@ -397,17 +403,17 @@ bin_reduce_kernel(const uint16_t *__restrict__ rkeys, const float *__restrict__ 
             const float vv[8] = {v0[u].x, v0[u].y, v0[u].z, v0[u].w, v1[u].x, v1[u].y, v1[u].z, v1[u].w};
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-                if (kk[e] < nf) add(kk[e], vv[e]);
+                if (kk[e] - lo < nf) add(kk[e] - lo, vv[e]);
         }
     }
     for (int i = (n8 << 3) + t; i < cnt; i += kReduceThreads) {
         const uint32_t k = keys[i];
-        if (k < nf) add(k, vs[i]);
+        if (k - lo < nf) add(k - lo, vs[i]);
     }
     if (FIXED) {
         // the overflow records of this slice (pass 1 finished: their count is final)
         const int no = min(__ldg(cursor + P), ocap);
-        const uint32_t c0 = b0 * static_cast<uint32_t>(d);
+        const uint32_t c0 = b0 * static_cast<uint32_t>(d) + lo;
         for (int i = t; i < no; i += kReduceThreads) {
             const uint2 r = __ldg(orec + i);
             if (r.x >= c0 && r.x - c0 < nf) add(r.x - c0, __uint_as_float(r.y));
@@ -450,12 +456,12 @@ int rows_per_lane(int64_t n, int64_t nnz, int T) {
     return r;
 }
 
-// log2 of the buckets per slice: the largest power of two SB whose SB d cells fit the
-// 128 KB slice (kSliceFloats fp32 cells, or half as many int64 cells with `fixed`).
-int slice_log2(int d, bool fixed = false) {
-    const int64_t cells = fixed ? kSliceFloats / 2 : kSliceFloats;
+// log2 of the buckets per slice: the largest power of two SB with SB d <= kSliceFloats.
+// The fixed-point form bins by the same slices (fewer slices keep pass 1's runs long) and
+// sums each in kFixedCells parts.
+int slice_log2(int d) {
     int l = 0;
-    while ((2LL << l) * d <= cells) ++l;
+    while ((2LL << l) * d <= kSliceFloats) ++l;
     return l;
 }
 
@@ -466,7 +472,7 @@ struct BinPlan {
 
 BinPlan bin_plan(int64_t n, int d, int64_t B, int64_t nnz, int ctas, bool fixed = false) {
     BinPlan L;
-    L.sb_log2 = slice_log2(d, fixed);
+    L.sb_log2 = slice_log2(d);
     L.P = static_cast<int>((B + (1LL << L.sb_log2) - 1) >> L.sb_log2);
     const int sms = num_sms() > 0 ? num_sms() : 148;
     const int G = ctas > 0 ? ctas : 2 * sms;
@@ -513,8 +519,9 @@ cudaError_t launch_bin_pass(const BinPlan &L, const BinArgs &a, cudaStream_t str
 }  // namespace
 
 bool binned_supported(int64_t n, int d, int64_t B, bool fixed) {
-    if (d > (fixed ? kSliceFloats / 2 : kSliceFloats) || n <= 0) return false;
-    const int l = slice_log2(d, fixed);
+    (void)fixed;
+    if (d > kSliceFloats || n <= 0) return false;
+    const int l = slice_log2(d);
     const int64_t P = (B + (1LL << l) - 1) >> l;
     return P <= kMaxSlices && static_cast<uint64_t>(P << l) * static_cast<uint64_t>(d) < (1ull << 32);
 }
@@ -565,15 +572,18 @@ cudaError_t launch_sketch_csr_binned(const int *row_ptr, const int *col_idx, con
         default: e = launch_bin_pass<16>(L, a, stream); break;
     }
     if (e != cudaSuccess) return e;
-    const size_t smem2 = (static_cast<size_t>(1) << L.sb_log2) * d * (fixed ? sizeof(unsigned long long) : sizeof(float));
+    const size_t slice_cells = (static_cast<size_t>(1) << L.sb_log2) * d;
+    const int parts = fixed ? static_cast<int>((slice_cells + kFixedCells - 1) / kFixedCells) : 1;
+    const size_t smem2 = fixed ? std::min<size_t>(slice_cells, kFixedCells) * sizeof(unsigned long long)
+                               : slice_cells * sizeof(float);
     auto reduce = fixed ? bin_reduce_kernel<true> : bin_reduce_kernel<false>;
     if ((e = cudaFuncSetAttribute(reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem2))) !=
         cudaSuccess)
         return e;
-    e = launch_after_previous(reduce, dim3(L.P), dim3(kReduceThreads), smem2, stream,
+    e = launch_after_previous(reduce, dim3(L.P * parts), dim3(kReduceThreads), smem2, stream,
                               static_cast<const uint16_t *>(a.rkeys), static_cast<const float *>(a.rvals), a.cursor,
                               L.P, L.scap, L.sb_log2, d, B, SX, clear ? 0 : 1, a.ocap,
-                              static_cast<const uint2 *>(a.orec), static_cast<const int *>(maxbits), nnz);
+                              static_cast<const uint2 *>(a.orec), static_cast<const int *>(maxbits), nnz, parts);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess && fixed)
         e = launch_add_nonfinite(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, maxbits, SX, stream);
