@@ -22,7 +22,9 @@
 //                   list (normally empty) with global atomics.
 // DRAM traffic: the CSR once, 6 bytes of record per nonzero written and read once, SX
 // written once.  Sums are fp32 in an order that depends on timing, as with the atomic
-// scatter.
+// scatter -- or, in the deterministic mode's form, the exact int64 fixed-point sums of
+// the deterministic scatter (two reduce CTAs per slice, one half of its cells each, after
+// a max-|x| pass), which do not depend on the order.
 #include <algorithm>
 
 #include "cg_internal.cuh"
