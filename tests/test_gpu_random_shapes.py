@@ -89,3 +89,21 @@ def test_random_shape_every_scatter(k):
         Yb = plan.apply_csr(rp, ci, v).cpu().numpy()
         plan.check()
         assert rel(Yb, Yo) < FP32_TOL, ("bf16x3", n, d, m, B)
+
+
+@pytest.mark.parametrize("k", range(24))
+def test_random_shape_plain_and_adjoint(k):
+    """The plain product G~ X and the adjoint at the stored entries, dX_k = sigma(i)
+    (G^T dY)[h(i), col_k], on the same random shapes."""
+    n, d, m, B, seed, max_row, offset = draw_case(k)
+    X = synth.csr_ragged(n, d, seed=seed, max_row=max_row)
+    rp = torch.from_numpy(X.row_ptr.astype(np.int32)).cuda()
+    ci = torch.from_numpy(X.col_idx.astype(np.int32)).cuda()
+    v = torch.from_numpy(X.vals.astype(np.float32)).cuda()
+    plan = cg().CountGauss(n, d, m, B, seed, row_offset=offset)
+    Yp = plan.plain_csr(rp, ci, v).cpu().numpy()
+    dYn = np.random.default_rng(seed).standard_normal((m, d)).astype(np.float32)
+    dXv = plan.adjoint(torch.from_numpy(dYn).cuda(), rp, ci).cpu().numpy()
+    plan.check()
+    assert rel(Yp, oracle.plain_csr(seed, n, d, m, X.row_ptr, X.col_idx, X.vals, row_offset=offset)) < FP32_TOL
+    assert rel(dXv, oracle.adjoint_csr(seed, n, m, B, X.row_ptr, X.col_idx, dYn, row_offset=offset)) < FP32_TOL
