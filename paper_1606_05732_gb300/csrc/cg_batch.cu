@@ -228,7 +228,7 @@ batch_kernel(const BatchInst *__restrict__ insts, const BatchItem *__restrict__ 
         float *part = I.partials + static_cast<size_t>(item.a) * I.m * I.d;
         for (int m0 = 0; m0 < I.m; m0 += kFfmaBM)
             for (int n0 = 0; n0 < I.d; n0 += FfmaShape<4>::BN) {
-                ffma_block<4, true, false>(I.SX, I.m, I.d, static_cast<int64_t>(I.B), I.key, s0, s1, m0, n0, (I.d & 3) == 0,
+                ffma_block<4, true>(I.SX, I.m, I.d, static_cast<int64_t>(I.B), I.key, s0, s1, m0, n0, (I.d & 3) == 0,
                                     part, raw);
                 __syncthreads();
             }
