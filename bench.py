@@ -254,6 +254,8 @@ def cpu_baselines(X, w):
     (if that takes under about two minutes: else on a fraction of the rows and of G's
     columns, which scales both stages alike)."""
     import oracle
+
+    from paper_1606_05732_gb300 import synth
     oracle.build()
     cores = host_cores()
     t0 = time.perf_counter()
@@ -262,11 +264,21 @@ def cpu_baselines(X, w):
     est_one = t_all * cores
     frac = 1.0 if est_one < 120 else 0.25
     dt, k1 = oracle_fraction_step(X, w, frac, 1)
+    # the plain product on a sample of its output rows: row r of G~.X needs row r of G~
+    # only, so the time of all m rows is the sample's times m / rows (extrapolated)
+    rows = synth.sample_rows(w["m"], w["seed"], 2)
+    t0 = time.perf_counter()
+    oracle.plain_csr(w["seed"], X.n, X.d, w["m"], X.row_ptr, X.col_idx, X.vals, rows=rows)
+    tp = (time.perf_counter() - t0) * w["m"] / rows.size
     return {"value": X.nnz / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"the whole workload (n={X.n}, nnz={X.nnz}), FP64, {cores} host threads, {t_all:.2f} s",
             "one_core": {"value": k1 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": ("the whole workload" if frac == 1.0 else f"{frac} of the rows and of the columns of G")
-                         + f", FP64, one thread, {dt:.2f} s"}}
+                         + f", FP64, one thread, {dt:.2f} s"},
+            "plain_one_core": {"value": X.nnz / tp, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "extrapolated": True,
+                               "sample": f"rows {rows.tolist()} of the plain product G~.X, FP64, one thread, "
+                                         f"{tp * rows.size / w['m']:.2f} s, scaled to all {w['m']} rows"}}
 
 
 # ------------------------------------------------------------------------------------

@@ -51,6 +51,21 @@ def test_oracle_fraction_step_does_that_fraction_of_the_work():
     assert dt > 0 and k1 == int(X.row_ptr[X.n // 4])
 
 
+def test_cpu_baselines_time_the_oracle_and_the_plain_product():
+    """The bench's cpu_baseline: the oracle on all host cores and on one, and the plain
+    product's oracle on a sample of output rows, labelled as extrapolated to all m rows."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1606_05732_gb300 import synth
+    X, w = synth.workload_csr("small_n65536_d16")
+    r = bench.cpu_baselines(X, w)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] == bench.host_cores()
+    assert r["one_core"]["cores"] == 1 and r["one_core"]["value"] > 0
+    p = r["plain_one_core"]
+    assert p["extrapolated"] is True and p["cores"] == 1 and p["value"] > 0
+    assert "scaled to all 8 rows" in p["sample"]
+
+
 def test_reference_arm_other_ranks_print_nothing():
     env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT="29511")
     assert _run("--gpus", "2", env=env) == []
