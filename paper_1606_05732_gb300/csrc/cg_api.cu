@@ -445,7 +445,8 @@ cg_status run_sketch_csr(cg_plan *p, const int32_t *row_ptr, const int32_t *col_
                                                     static_cast<uint32_t>(p->B), static_cast<int>(nnz),
                                                     make_key(p->seed), p->row_offset, SX, status_word(ws),
                                                     region(ws, L.c_off), static_cast<int>(p->sketch_ctas),
-                                                    p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st, clear));
+                                                    p->scatter_rows, timing_pair(p, CG_KERNEL_SKETCH), st, clear,
+                                                    !host_mapped));
     if (use_partition(*p))
         return from_cuda(launch_sketch_csr_partitioned(
             row_ptr, col_idx, vals, static_cast<int>(p->n), p->d, static_cast<uint32_t>(p->B), static_cast<int>(nnz),

@@ -146,8 +146,10 @@ cudaError_t launch_sketch_csr_fixed(const int *row_ptr, const int *col_idx, cons
 int one_pass_rows(const cg_plan &p, int64_t nnz);
 
 // ---- deferred scatter (cg_sketch_defer.cu) -----------------------------------------
-// SX split at bucket B/2: one CSR pass reduces the lower half and writes the rest as
+// SX split at bucket bsplit: one CSR pass reduces the lower part and writes the rest as
 // records, a second pass reduces the records (for an SX larger than the L2 holds).
+// staged_ok: the CSR arrays are device memory, so pass 1 may stage them in shared memory
+// with bulk copies (when col_idx and vals are 16-byte aligned and B d <= 2^31).
 bool deferred_supported(int64_t B, int d);
 // CTAs of the deferred scatter for n rows and nnz nonzeros (`ctas` > 0: as given;
 // `rows`: the CG_OPT_SCATTER_ROWS option).
@@ -156,7 +158,7 @@ size_t sketch_deferred_scratch_bytes(int64_t nnz, int ctas);
 cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                        uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                        void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
-                                       bool clear = true);
+                                       bool clear = true, bool staged_ok = true);
 // The same with int64 row offsets (each warp chunk rebased to its first nonzero, record
 // indices and per-CTA counts 64-bit).
 cudaError_t launch_sketch_csr_deferred_i64(const long long *row_ptr, const int *col_idx, const float *vals, int n,

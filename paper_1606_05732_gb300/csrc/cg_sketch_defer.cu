@@ -24,6 +24,7 @@
 
 #include "cg_internal.cuh"
 #include "cg_scatter.cuh"
+#include "cg_tc.cuh"
 
 namespace cg {
 
@@ -282,6 +283,251 @@ split_pass_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_id
     if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
 }
 
+// ---- pass 1 with each chunk's nonzeros staged in shared memory ----------------------
+// The same pass for int offsets and device-resident, 16-byte aligned col_idx and vals
+// (B d <= 2^31).  Once a warp has its chunk's row offsets, one lane starts two bulk
+// copies (cp.async.bulk, completion on a per-warp mbarrier) of the chunk's col_idx and
+// vals into shared memory, from the 16-byte boundary at or below the first nonzero up
+// to the last boundary at or below the end (the ragged tail of at most three nonzeros
+// is loaded by plain loads); while the copies are in flight the warp hashes its rows and
+// builds the row map, so the hashing hides the load latency, and the sweep then reads
+// its operands from shared memory.  A row's bucket and sign are kept as one word,
+// h d with the sign in bit 31.  Chunks of more than kStageCap nonzeros (past the 16-byte
+// boundary below the first) read their nonzeros from global memory as in the plain pass.
+constexpr int kStageCap = 384;
+constexpr uint32_t kStageWaitPolls = 1u << 22;  // bounded wait for a chunk's copies
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> this CTA's shared memory (dst, src 16-byte aligned, bytes a
+// multiple of 16), completing `bytes` transactions on the mbarrier at `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint32_t bar,
+                                              uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+        : "memory");
+}
+
+// The sweep of one chunk: STAGED reads nonzero k's column and value at s_col / s_val
+// [k - kbase], else from global memory; a row is found in the row map (MAPPED) or by
+// binary search over the offsets in s_rp.  Reduction or record as in split_chunk.
+template <int ROWS, bool STAGED, bool MAPPED>
+__device__ __forceinline__ void split_sweep(const int *__restrict__ col_idx, const float *__restrict__ vals,
+                                            const int *s_col, const int *s_val, int kbase, int beg, int end, int d,
+                                            float *__restrict__ SX, uint32_t lo_cell, uint2 *__restrict__ region,
+                                            int cap, int *s_count, const uint32_t *s_hw, const uint8_t *s_map,
+                                            const int *s_rp, uint64_t pol, int &bad) {
+    const int lane = threadIdx.x & 31;
+    for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
+        int col[kScatterUnroll];
+        float v[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const int k = k0 + u * 32 + lane;
+            col[u] = -1;
+            v[u] = 0.0f;
+            if (k0 + u * 32 < end && k < end) {  // first test warp-uniform
+                if constexpr (STAGED) {
+                    col[u] = s_col[k - kbase];
+                    v[u] = __int_as_float(s_val[k - kbase]);
+                } else {
+                    col[u] = ld_stream_i32(col_idx + k, pol);
+                    v[u] = ld_stream_f32(vals + k, pol);
+                }
+            }
+        }
+        bool dfr[kScatterUnroll];
+        uint32_t cell[kScatterUnroll];
+        float x[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const int k = k0 + u * 32 + lane;
+            dfr[u] = false;
+            cell[u] = 0;
+            x[u] = 0.0f;
+            if (k < end) {
+                int lo = 0;
+                if constexpr (MAPPED) {
+                    lo = s_map[k - beg];
+                } else {
+#pragma unroll
+                    for (int step = ROWS / 2; step > 0; step >>= 1)
+                        if (s_rp[lo + step] <= k) lo += step;
+                }
+                const int j = col[u];
+                const uint32_t hw = s_hw[lo];
+                if (static_cast<unsigned>(j) < static_cast<unsigned>(d)) {
+                    const uint32_t base = hw & 0x7fffffffu;
+                    cell[u] = base + static_cast<uint32_t>(j);
+                    x[u] = __uint_as_float(__float_as_uint(v[u]) ^ (hw & 0x80000000u));  // sigma x, exactly
+                    if (base < lo_cell)
+                        atomicAdd(SX + cell[u], x[u]);
+                    else
+                        dfr[u] = true;
+                } else {
+                    bad = 1;
+                }
+            }
+        }
+        unsigned mask[kScatterUnroll];
+        int total = 0;
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            mask[u] = __ballot_sync(0xffffffffu, dfr[u]);
+            total += __popc(mask[u]);
+        }
+        if (total == 0) continue;  // warp-uniform
+        int at0 = 0;
+        if (lane == 0) at0 = atomicAdd(s_count, total);
+        at0 = __shfl_sync(0xffffffffu, at0, 0);
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            if (dfr[u]) {
+                const int at = at0 + __popc(mask[u] & below);
+                if (at < cap)
+                    st_stream_u2(region + at, make_uint2(cell[u], __float_as_uint(x[u])), pol);
+                else
+                    bad = 1;
+            }
+            at0 += __popc(mask[u]);
+        }
+    }
+    __syncwarp();
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads, 5)
+split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                         const float *__restrict__ vals, int n, int d, uint32_t B, int nnz, Key key,
+                         int64_t row_offset, float *__restrict__ SX, uint32_t lo_cell, int rows_per_cta,
+                         uint2 *__restrict__ records, int *__restrict__ counts, int *__restrict__ status) {
+    constexpr int R = ROWS / 32;
+    static_assert(ROWS + 1 <= 2 * kStageCap && ROWS <= 256, "row offsets fit the staging area; rows fit a byte");
+    __shared__ __align__(16) int s_stage[kWarps][2 * kStageCap];  // col_idx | vals, or the row offsets
+    __shared__ uint32_t s_hw[kWarps][ROWS];
+    __shared__ uint8_t s_map[kWarps][kMapCap];
+    __shared__ __align__(8) uint64_t s_bar[kWarps];
+    __shared__ int s_count;
+    const int w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int r0 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(blockIdx.x) * rows_per_cta));
+    const int r1 = static_cast<int>(min(static_cast<int64_t>(n), static_cast<int64_t>(r0) + rows_per_cta));
+    const int rec_lo = __ldg(row_ptr + r0);
+    const int rec_hi = __ldg(row_ptr + r1);
+    if (rec_lo < 0 || rec_hi > nnz || rec_lo > rec_hi) {  // uniform over the CTA
+        if (threadIdx.x == 0) {
+            counts[blockIdx.x] = 0;
+            atomicOr(status, kStatusBounds);
+        }
+        return;
+    }
+    const uint32_t bar = tc::smem_u32(&s_bar[w]);
+    if (lane == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_mbar_init();
+    }
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const uint64_t pol = l2_evict_first_policy();
+    uint2 *region = records + rec_lo;
+    const int cap = rec_hi - rec_lo;
+    uint32_t phase = 0;
+    int bad = 0, late = 0;
+    for (int first = r0 + w * ROWS; first < r1; first += kWarps * ROWS) {
+        if (first != r0 + w * ROWS) {  // the previous chunk's shared-memory accesses before new copies
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+        }
+        const int last = min(first + ROWS, r1);
+        const int end = __ldg(row_ptr + last);
+        int rp[R], nx[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = first + r * 32 + lane;
+            rp[r] = i < last ? ld_stream_i32(row_ptr + i, pol) : end;
+        }
+        bool ordered = true;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {  // nx[r]: the offset after row r*32 + lane
+            const int up = __shfl_sync(0xffffffffu, r + 1 < R ? rp[r + 1 < R ? r + 1 : r] : end, 0);
+            const int dn = __shfl_down_sync(0xffffffffu, rp[r], 1);
+            nx[r] = lane == 31 ? up : dn;
+            ordered &= rp[r] <= nx[r];
+        }
+        const int beg = __shfl_sync(0xffffffffu, rp[0], 0);
+        if (end > nnz || beg < 0 || !__all_sync(0xffffffffu, ordered)) {  // malformed offsets: skip the chunk
+            bad = 1;
+            continue;
+        }
+        const int kbase = beg & ~3;
+        const bool staged = end - kbase <= kStageCap;  // warp-uniform
+        const bool mapped = end - beg <= kMapCap;
+        int nb = 0;
+        if (staged) {
+            const int end_lo = end & ~3;
+            nb = end_lo > kbase ? end_lo - kbase : 0;
+            if (nb > 0 && lane == 0) {
+                mbar_expect_tx(bar, 8u * static_cast<uint32_t>(nb));
+                bulk_copy_g2s(&s_stage[w][0], col_idx + kbase, 4u * nb, bar, pol);
+                bulk_copy_g2s(&s_stage[w][kStageCap], vals + kbase, 4u * nb, bar, pol);
+            }
+            const int k = max(kbase + nb, beg) + lane;  // the ragged tail: at most three nonzeros
+            if (k < end) {
+                s_stage[w][k - kbase] = ld_stream_i32(col_idx + k, pol);
+                s_stage[w][kStageCap + k - kbase] = __float_as_int(ld_stream_f32(vals + k, pol));
+            }
+        } else if (!mapped) {  // row offsets for the binary search, in the unused staging area
+#pragma unroll
+            for (int r = 0; r < R; ++r) s_stage[w][r * 32 + lane] = rp[r];
+            if (lane == 0) s_stage[w][ROWS] = end;
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {  // while the copies are in flight
+            const int i = first + r * 32 + lane;
+            uint32_t hw = 0;
+            if (i < last) {
+                uint32_t h;
+                float sg;
+                hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
+                hw = h * static_cast<uint32_t>(d) | (sg < 0.0f ? 0x80000000u : 0u);
+            }
+            s_hw[w][r * 32 + lane] = hw;
+        }
+        if (mapped) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                for (int k = rp[r]; k < nx[r]; ++k) s_map[w][k - beg] = static_cast<uint8_t>(r * 32 + lane);
+        }
+        __syncwarp();
+        if (nb > 0) {
+            if (!__all_sync(0xffffffffu, tc::mbar_wait_bounded(bar, phase, kStageWaitPolls))) {
+                late = 1;  // give up on this warp's rows; let the copies land before the CTA ends
+                tc::mbar_wait_bounded(bar, phase, kStageWaitPolls);
+                break;
+            }
+            phase ^= 1u;
+        }
+        if (staged)
+            split_sweep<ROWS, true, true>(col_idx, vals, s_stage[w], s_stage[w] + kStageCap, kbase, beg, end, d, SX,
+                                          lo_cell, region, cap, &s_count, s_hw[w], s_map[w], nullptr, pol, bad);
+        else if (mapped)
+            split_sweep<ROWS, false, true>(col_idx, vals, nullptr, nullptr, 0, beg, end, d, SX, lo_cell, region, cap,
+                                           &s_count, s_hw[w], s_map[w], nullptr, pol, bad);
+        else
+            split_sweep<ROWS, false, false>(col_idx, vals, nullptr, nullptr, 0, beg, end, d, SX, lo_cell, region,
+                                            cap, &s_count, s_hw[w], nullptr, s_stage[w], pol, bad);
+    }
+    if (bad) atomicOr(status, kStatusBounds);
+    if (late) atomicOr(status, kStatusTimeout);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = s_count;
+}
+
 // Pass 2: CTA c reduces the counts[c] records of its region into SX.  First each CTA asks
 // for its share of the upper half of SX (cells [lo_cell, cells)) to be brought into L2,
 // where pass 1 left the lower half (a small gain: at the ladder size the pass is bound by
@@ -380,10 +626,24 @@ int sketch_deferred_ctas(int ctas, int64_t n, int64_t nnz, int rows) {
 
 namespace {
 
+// The staged pass 1 needs five CTAs' 41 KB of shared memory on an SM: ask for the
+// largest shared-memory carveout.
+template <int ROWS>
+void launch_staged(int grid, const int *row_ptr, const int *col_idx, const float *vals, int n, int d, uint32_t B,
+                   int nnz, Key key, int64_t row_offset, float *SX, uint32_t lo_cell, int rows_per_cta,
+                   uint2 *records, int *counts, int *status, cudaStream_t stream) {
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        split_pass_staged_kernel<ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    (void)attr;  // a preference only
+    split_pass_staged_kernel<ROWS><<<grid, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
+                                                                  row_offset, SX, lo_cell, rows_per_cta, records,
+                                                                  counts, status);
+}
+
 template <typename RP>
 cudaError_t sketch_deferred(const RP *row_ptr, const int *col_idx, const float *vals, int n, int d, uint32_t B,
                             RP nnz, Key key, int64_t row_offset, float *SX, int *status, void *scratch, int ctas,
-                            int rows, const EventPair *ev, cudaStream_t stream, bool clear) {
+                            int rows, const EventPair *ev, cudaStream_t stream, bool clear, bool staged_ok) {
     cudaError_t e = clear ? cudaMemsetAsync(SX, 0, static_cast<size_t>(B) * d * sizeof(float), stream) : cudaSuccess;
     if (e != cudaSuccess || n == 0) return e;
     const int G = sketch_deferred_ctas(ctas, n, nnz, rows);
@@ -398,6 +658,34 @@ cudaError_t sketch_deferred(const RP *row_ptr, const int *col_idx, const float *
     RP *counts = reinterpret_cast<RP *>(static_cast<char *>(scratch) + align256(static_cast<size_t>(nnz) * sizeof(uint2)));
     const uint32_t bsplit = deferred_split(B, d);
     record(ev, true, stream);
+    if constexpr (sizeof(RP) == 4) {
+        if (staged_ok && ((reinterpret_cast<uintptr_t>(col_idx) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0 &&
+            static_cast<uint64_t>(B) * static_cast<uint64_t>(d) <= (1ull << 31)) {
+            const uint32_t lo_cell = bsplit * static_cast<uint32_t>(d);
+            switch (H) {
+                case 256:
+                    launch_staged<256>(used, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, lo_cell,
+                                       rows_per_cta, records, counts, status, stream);
+                    break;
+                case 128:
+                    launch_staged<128>(used, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, lo_cell,
+                                       rows_per_cta, records, counts, status, stream);
+                    break;
+                case 64:
+                    launch_staged<64>(used, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, lo_cell,
+                                      rows_per_cta, records, counts, status, stream);
+                    break;
+                default:
+                    launch_staged<32>(used, row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, lo_cell,
+                                      rows_per_cta, records, counts, status, stream);
+                    break;
+            }
+            replay_records_kernel<RP><<<used, kThreads, 0, stream>>>(row_ptr, n, rows_per_cta, records, counts,
+                                                                     lo_cell, B * static_cast<uint32_t>(d), SX);
+            record(ev, false, stream);
+            return cudaGetLastError();
+        }
+    }
     switch (H) {
         case 256:
             split_pass_kernel<256, RP><<<used, kThreads, 0, stream>>>(row_ptr, col_idx, vals, n, d, B, nnz, key,
@@ -432,9 +720,9 @@ cudaError_t sketch_deferred(const RP *row_ptr, const int *col_idx, const float *
 cudaError_t launch_sketch_csr_deferred(const int *row_ptr, const int *col_idx, const float *vals, int n, int d,
                                        uint32_t B, int nnz, Key key, int64_t row_offset, float *SX, int *status,
                                        void *scratch, int ctas, int rows, const EventPair *ev, cudaStream_t stream,
-                                       bool clear) {
+                                       bool clear, bool staged_ok) {
     return sketch_deferred<int>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, status, scratch, ctas, rows,
-                                ev, stream, clear);
+                                ev, stream, clear, staged_ok);
 }
 
 cudaError_t launch_sketch_csr_deferred_i64(const long long *row_ptr, const int *col_idx, const float *vals, int n,
@@ -442,7 +730,7 @@ cudaError_t launch_sketch_csr_deferred_i64(const long long *row_ptr, const int *
                                            int *status, void *scratch, int ctas, int rows, const EventPair *ev,
                                            cudaStream_t stream, bool clear) {
     return sketch_deferred<long long>(row_ptr, col_idx, vals, n, d, B, nnz, key, row_offset, SX, status, scratch, ctas,
-                                      rows, ev, stream, clear);
+                                      rows, ev, stream, clear, false);
 }
 
 }  // namespace cg
