@@ -120,7 +120,8 @@ def philox_words(seed: int, tag: int, idx0: int, count: int) -> np.ndarray:
 
 def hash_sign(seed: int, B: int, row0: int, count: int):
     """CountSketch bucket h(i) in [0,B) and sign sigma(i) in {-1,+1} for global rows
-    row0..row0+count-1 (Section 1.1; Section 7)."""
+    row0..row0+count-1 (Section 1.1; Section 7): word i mod 4 of the tag-0 call at
+    floor(i/4), its multiply-high by B and its lowest bit."""
     lib = _load()
     h = np.zeros(count, np.int64)
     s = np.zeros(count, np.int32)

@@ -23,8 +23,9 @@
  *   - Random words come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  *     Random Numbers: As Easy as 1, 2, 3", SC'11): key = (lo32(seed), hi32(seed)),
  *     counter = (lo32(idx), hi32(idx), tag, 0).
- *   - tag 0, idx = global row i: h(i) = floor(w0 * B / 2^32), sigma(i) = -1 if the
- *     top bit of w1 is set, else +1.
+ *   - tag 0, idx = floor(i / 4) for global row i: with w = word (i mod 4) of that
+ *     call, h(i) = floor(w * B / 2^32) and sigma(i) = -1 if the lowest bit of w is set,
+ *     else +1 (one call serves four consecutive rows).
  *   - uniform u(w) = (2 * (w >> 9) + 1) * 2^-24, an odd multiple of 2^-24 in (0,1).
  *   - an R x C Gaussian matrix with tag t: entry (r, c) is lane (r mod 4) of the four
  *     Box-Muller normals from the Philox call at idx = c * ceil(R/4) + floor(r/4):
@@ -95,15 +96,22 @@ void orc_philox_words(uint64_t seed, uint32_t tag, uint64_t idx0, int64_t count,
 
 /* ---------------------------------------------------------------------------
  * Column hash h and sign sigma of the CountSketch (Section 1.1; Section 7).
- * h(i) is uniform on [0, B) (multiply-high of a uniform 32-bit word, bias at most
- * B / 2^32); sigma(i) is a fair sign from an independent bit.
+ * Row i takes word (i mod 4) of the tag-0 call at idx floor(i/4).  h(i) is uniform on
+ * [0, B) (multiply-high of a uniform 32-bit word, bias at most B / 2^32); sigma(i) is
+ * its lowest bit, which is independent of h(i) when B is a power of two (h then reads
+ * only the top log2(B) bits) and otherwise tilts P(sigma = -1 | h) from 1/2 by at most
+ * B / 2^32 (B < 2^31: each bucket is an interval of at least two words, whose odd
+ * words are half of them up to one).  Different rows use different words, so all
+ * choices are independent.
  * ------------------------------------------------------------------------- */
 static void orc_hash_sign_one(uint64_t seed, int64_t B, int64_t i, int64_t *h, int *sigma)
 {
     uint32_t w[4];
-    orc_words(seed, (uint64_t)i, ORC_TAG_HASH, w);
-    *h = (int64_t)(((uint64_t)w[0] * (uint64_t)B) >> 32);
-    *sigma = (w[1] >> 31) ? -1 : 1;
+    uint32_t x;
+    orc_words(seed, (uint64_t)i / 4u, ORC_TAG_HASH, w);
+    x = w[(uint64_t)i % 4u];
+    *h = (int64_t)(((uint64_t)x * (uint64_t)B) >> 32);
+    *sigma = (x & 1u) ? -1 : 1;
 }
 
 void orc_hash_sign(uint64_t seed, int64_t B, int64_t row0, int64_t count, int64_t *h, int32_t *sigma)

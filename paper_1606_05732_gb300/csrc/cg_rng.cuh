@@ -6,7 +6,8 @@
 // random matrix is ever stored:
 //   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key (lo32(seed), hi32(seed)),
 //   counter (lo32(idx), hi32(idx), tag, 0).
-//   tag 0, idx = global row i:  h(i) = floor(w0 * B / 2^32),  sigma(i) = bit31(w1) ? -1 : +1.
+//   tag 0, idx = floor(i / 4) for global row i, w = word i mod 4 of the call:
+//     h(i) = floor(w * B / 2^32),  sigma(i) = bit0(w) ? -1 : +1  (four rows per call).
 //   uniform u(w) = (2 (w >> 9) + 1) 2^-24, exact in fp32, never 0 or 1.
 //   Box-Muller quadruple of one call: sqrt(-2 ln u0) (cos, sin)(2 pi u1),
 //                                     sqrt(-2 ln u2) (cos, sin)(2 pi u3).
@@ -51,11 +52,18 @@ __device__ __forceinline__ uint4 stream_words(Key k, uint64_t idx, uint32_t tag)
     return philox10(make_uint4(static_cast<uint32_t>(idx), static_cast<uint32_t>(idx >> 32), tag, 0u), k);
 }
 
+// The hash word of global row i: word i mod 4 of the tag-0 call at floor(i / 4).
+__device__ __forceinline__ uint32_t hash_word(Key k, uint64_t row) {
+    const uint4 w = stream_words(k, row >> 2, kTagHash);
+    const uint32_t q = static_cast<uint32_t>(row) & 3u;
+    return q == 0u ? w.x : q == 1u ? w.y : q == 2u ? w.z : w.w;
+}
+
 // Bucket and sign of global row i for a sketch with B rows (B < 2^32).
 __device__ __forceinline__ void hash_sign(Key k, uint64_t row, uint32_t B, uint32_t &h, float &s) {
-    const uint4 w = stream_words(k, row, kTagHash);
-    h = __umulhi(w.x, B);
-    s = (w.y & 0x80000000u) ? -1.0f : 1.0f;
+    const uint32_t w = hash_word(k, row);
+    h = __umulhi(w, B);
+    s = (w & 1u) ? -1.0f : 1.0f;
 }
 
 // u(w) = (2 (w >> 9) + 1) 2^-24, formed without an integer-to-float conversion: the float

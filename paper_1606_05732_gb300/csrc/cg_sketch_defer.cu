@@ -291,8 +291,9 @@ split_pass_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_id
 // to the last boundary at or below the end (the ragged tail of at most three nonzeros
 // is loaded by plain loads); while the copies are in flight the warp hashes its rows and
 // builds the row map, so the hashing hides the load latency, and the sweep then reads
-// its operands from shared memory.  A row's bucket and sign are kept as one word,
-// h d with the sign in bit 31.  Chunks of more than kStageCap nonzeros (past the 16-byte
+// its operands from shared memory.  Each lane hashes four consecutive rows with one
+// Philox call (the words of a call serve four rows), and a row's bucket and sign are
+// kept as one word, h d with the sign in bit 31.  Chunks of more than kStageCap nonzeros (past the 16-byte
 // boundary below the first) read their nonzeros from global memory as in the plain pass.
 constexpr int kStageCap = 384;
 constexpr uint32_t kStageWaitPolls = 1u << 22;  // bounded wait for a chunk's copies
@@ -486,17 +487,23 @@ split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict_
             for (int r = 0; r < R; ++r) s_stage[w][r * 32 + lane] = rp[r];
             if (lane == 0) s_stage[w][ROWS] = end;
         }
+        {  // while the copies are in flight: one Philox call per lane hashes four rows
+            const int64_t g0 = row_offset + first;   // global row of chunk row 0
+            const int64_t c0 = g0 >> 2;                // its call
+            const int calls = static_cast<int>(((g0 + (last - first) - 1) >> 2) - c0 + 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {  // while the copies are in flight
-            const int i = first + r * 32 + lane;
-            uint32_t hw = 0;
-            if (i < last) {
-                uint32_t h;
-                float sg;
-                hash_sign(key, static_cast<uint64_t>(row_offset + i), B, h, sg);
-                hw = h * static_cast<uint32_t>(d) | (sg < 0.0f ? 0x80000000u : 0u);
+            for (int t = 0; t < (ROWS + 127) / 128 + 1; ++t) {  // the last round only where g0 % 4 != 0
+                const int c = t * 32 + lane;
+                if (t * 32 < calls && c < calls) {
+                    const uint4 wd = stream_words(key, static_cast<uint64_t>(c0 + c), kTagHash);
+                    const int q0 = static_cast<int>(4 * (c0 + c) - g0);  // chunk row of the call's word 0
+                    const uint32_t ws[4] = {wd.x, wd.y, wd.z, wd.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (q0 + j >= 0 && q0 + j < last - first)
+                            s_hw[w][q0 + j] = __umulhi(ws[j], B) * static_cast<uint32_t>(d) | (ws[j] << 31);
+                }
             }
-            s_hw[w][r * 32 + lane] = hw;
         }
         if (mapped) {
 #pragma unroll

@@ -36,7 +36,8 @@ def build():
     out["philox_words"] = {"cite": "Philox4x32-10 (Salmon et al., SC'11); key (lo32, hi32 of seed), "
                                    "counter (lo32 idx, hi32 idx, tag, 0)", "cases": words}
     h, s = oracle.hash_sign(1, 4096, 0, 16)
-    out["hash_sign"] = {"cite": "Section 1.1 / Section 7: h(i) = floor(w0 B / 2^32), sigma(i) from bit 31 of w1",
+    out["hash_sign"] = {"cite": "Section 1.1 / Section 7: w = word i mod 4 of the tag-0 call at floor(i/4); "
+                                   "h(i) = floor(w B / 2^32), sigma(i) from the lowest bit of w",
                         "seed": 1, "B": 4096, "row0": 0, "h": [int(x) for x in h], "sigma": [int(x) for x in s]}
     g = oracle.gaussian_block(5, 1, 8, 0, 8, 0, 4)
     out["gaussian"] = {"cite": "Theorem 1 (unit-variance Gaussians): Box-Muller of the tag-1 stream, "

@@ -73,15 +73,22 @@ def test_stream_layout_words(triton_cases):
 # -----------------------------------------------------------------------------
 # Hash h and sign sigma (Section 1.1; Section 7).
 # -----------------------------------------------------------------------------
+@pytest.mark.parametrize("row0", [10**9, 10**9 + 3])
 @pytest.mark.parametrize("B", [1, 2, 3, 4096, 100003, 1 << 17, 1 << 18, (1 << 31) - 1, 1 << 32])
-def test_hash_is_multiply_high_of_word0(B):
+def test_hash_is_multiply_high_of_the_rows_word(B, row0):
+    """Row i reads word i mod 4 of the tag-0 call at floor(i/4): h = floor(w B / 2^32),
+    sigma from the word's lowest bit (rows from an offset that is not a multiple of 4
+    start inside a call)."""
     seed, n = 99, 2000
-    h, s = oracle.hash_sign(seed, B, 10**9, n)
-    w = oracle.philox_words(seed, 0, 10**9, n).astype(object)
+    h, s = oracle.hash_sign(seed, B, row0, n)
+    g0 = row0 // 4
+    w = oracle.philox_words(seed, 0, g0, (row0 + n - 1) // 4 - g0 + 1).astype(object)
     for t in range(n):
-        # floor(w0 * B / 2^32): h * 2^32 <= w0 * B < (h + 1) * 2^32
-        assert int(h[t]) * 2**32 <= int(w[t, 0]) * B < (int(h[t]) + 1) * 2**32
-        assert s[t] == (-1 if int(w[t, 1]) >> 31 else 1)
+        i = row0 + t
+        x = int(w[i // 4 - g0, i % 4])
+        # floor(x * B / 2^32): h * 2^32 <= x * B < (h + 1) * 2^32
+        assert int(h[t]) * 2**32 <= x * B < (int(h[t]) + 1) * 2**32
+        assert s[t] == (-1 if x & 1 else 1)
     assert h.min() >= 0 and h.max() < B
 
 
