@@ -50,11 +50,11 @@ UNIT = "nnz/s"
 
 # dram bytes (read + write) per launch of the scatter kernel(s) from one ncu capture of the
 # workload named, keyed by the sha256 of the kernel sources it was taken on (null once a
-# source changes).  nmf_n16M_d64: 537.01 MB read + 3.19 MB written, captured at full size.
-# ladder_n64M_d128 (the deferred pair, both kernels): pass 1 1190.3 MB read + 970.2 MB
-# written, replay 374.2 MB read + 116.3 MB written, captured at full size.
-NCU_TRAFFIC = {("2b7920603bafc59b", "nmf_n16M_d64"): 540_198_144,
-               ("77542edcce9920ae", "ladder_n64M_d128"): 2_650_968_576}
+# source changes).  nmf_n16M_d64: 536.78 MB read + 3.30 MB written, captured at full size.
+# ladder_n64M_d128 (the deferred pair, both kernels): pass 1 1103.0 MB read + 817.0 MB
+# written, replay 407.9 MB read + 305.9 MB written, captured at full size.
+NCU_TRAFFIC = {("6386e39308a65745", "nmf_n16M_d64"): 540_079_104,
+               ("94fa7123c15c82ad", "ladder_n64M_d128"): 2_633_828_864}
 
 
 def parse_args():
@@ -570,7 +570,7 @@ def scatter_kernels(args, B, d, dev):
         return "bin_pass_kernel+bin_reduce_kernel", ("cg_sketch_bin.cu", "cg_scatter.cuh", "cg_rng.cuh"), 5
     if args.scatter == "deferred" or (args.scatter == "auto" and args.scatter_passes == 0
                                       and 4 * B * d > 0.6 * l2 and B * d < (1 << 32)):
-        return "split_pass_kernel+replay_records_kernel", ("cg_sketch_defer.cu", "cg_scatter.cuh", "cg_rng.cuh"), 4
+        return "split_pass_staged_kernel+replay_records_kernel", ("cg_sketch_defer.cu", "cg_scatter.cuh", "cg_rng.cuh"), 4
     return "sketch_csr_kernel", ("cg_sketch.cu", "cg_scatter.cuh", "cg_rng.cuh"), 3
 
 

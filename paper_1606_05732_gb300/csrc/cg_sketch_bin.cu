@@ -110,6 +110,14 @@ __device__ __forceinline__ void copy_row_ptr(const int *row_ptr, int lo, int hi,
     cp_async_commit();
 }
 
+// Row of a tile held in slot q of thread t: with four or more rows per thread, groups
+// of four consecutive rows (so that one Philox call hashes a group, the four rows of a
+// call), else rows q kBinThreads + t.
+template <int RPL>
+__device__ __forceinline__ int bin_row(int q, int t) {
+    return RPL >= 4 ? 4 * ((q >> 2) * kBinThreads + t) + (q & 3) : q * kBinThreads + t;
+}
+
 template <int RPL>
 __global__ void __launch_bounds__(kBinThreads, RPL <= 8 ? 2 : 1) bin_pass_kernel(BinArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kBinThreads, RPL <= 8 ? 2 : 1) bin_pass_kernel
         int row_bad = 0;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
-            const int i = q * kBinThreads + t;
+            const int i = bin_row<RPL>(q, t);
             int k0 = 0, k1 = 0;
             if (tr0 + i < tr1) {
                 k0 = s_rp[i];
@@ -195,12 +203,32 @@ __global__ void __launch_bounds__(kBinThreads, RPL <= 8 ? 2 : 1) bin_pass_kernel
         for (int q = 0; q < RPL; ++q) {
             code[q] = 0;
             off[q] = 0;
-            if (len[q] > 0) {
-                uint32_t h;
-                float sg;
-                hash_sign(a.key, static_cast<uint64_t>(a.row_offset + tr0 + q * kBinThreads + t), a.B, h, sg);
-                code[q] = h | (sg < 0.0f ? 0x80000000u : 0u);
-                off[q] = atomicAdd(&s_cnt[h >> a.sb_log2], len[q]);
+        }
+        if (RPL >= 4 && ((a.row_offset + tr0) & 3) == 0) {  // uniform: a thread's groups of four are calls
+#pragma unroll
+            for (int g = 0; g < RPL / 4; ++g) {
+                if ((len[4 * g] | len[4 * g + 1] | len[4 * g + 2] | len[4 * g + 3]) == 0) continue;
+                const uint4 w = stream_words(
+                    a.key, static_cast<uint64_t>(a.row_offset + tr0 + bin_row<RPL>(4 * g, t)) >> 2, kTagHash);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (len[4 * g + j] == 0) continue;
+                    const uint32_t h = __umulhi(ws[j], a.B);
+                    code[4 * g + j] = h | (ws[j] << 31);  // sigma = -1 for an odd word
+                    off[4 * g + j] = atomicAdd(&s_cnt[h >> a.sb_log2], len[4 * g + j]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                if (len[q] > 0) {
+                    uint32_t h;
+                    float sg;
+                    hash_sign(a.key, static_cast<uint64_t>(a.row_offset + tr0 + bin_row<RPL>(q, t)), a.B, h, sg);
+                    code[q] = h | (sg < 0.0f ? 0x80000000u : 0u);
+                    off[q] = atomicAdd(&s_cnt[h >> a.sb_log2], len[q]);
+                }
             }
         }
         bad |= row_bad;
