@@ -51,10 +51,10 @@ UNIT = "nnz/s"
 # dram bytes (read + write) per launch of the scatter kernel(s) from one ncu capture of the
 # workload named, keyed by the sha256 of the kernel sources it was taken on (null once a
 # source changes).  nmf_n16M_d64: 536.78 MB read + 3.30 MB written, captured at full size.
-# ladder_n64M_d128 (the deferred pair, both kernels): pass 1 1103.0 MB read + 817.0 MB
-# written, replay 407.9 MB read + 305.9 MB written, captured at full size.
+# ladder_n64M_d128 (the deferred pair, both kernels): pass 1 1111.8 MB read + 465.4 MB
+# written, replay 408.0 MB read + 1.6 MB written, captured at full size.
 NCU_TRAFFIC = {("6386e39308a65745", "nmf_n16M_d64"): 540_079_104,
-               ("94fa7123c15c82ad", "ladder_n64M_d128"): 2_633_828_864}
+               ("83cefa2387ca0514", "ladder_n64M_d128"): 1_986_807_552}
 
 
 def parse_args():
@@ -297,6 +297,24 @@ def _time_calls(fn, reps, stream, warm=2):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def _time_each(fn, reps, stream, warm=2):
+    """Per-call ms of fn over `reps` calls (CUDA events on `stream` around each call, which
+    must synchronise before it returns): (median, mean)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts), sum(ts) / len(ts)
 
 
 def reduction_ceiling(dev, count, cells, reps=5):
@@ -687,8 +705,10 @@ def measure_workload(args, name, dev, rank=0, world=1, pg=None, steps=None, e2e=
                 pg.all_reduce(Y)
                 Y_h.copy_(Y, non_blocking=True)
 
-        e2e_steps = max(3, steps // 10)
-        e2e_ms = _time_calls(e2e_step, e2e_steps, stream)
+        # each call timed on its own (it synchronises) and the median taken: the host link
+        # is shared with a second GPU, and a burst of its traffic can slow a few calls
+        e2e_steps = max(7, steps // 10)
+        e2e_ms, e2e_mean = _time_each(e2e_step, e2e_steps, stream)
         if pg is not None:
             t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -696,11 +716,12 @@ def measure_workload(args, name, dev, rank=0, world=1, pg=None, steps=None, e2e=
         modes = {}  # the two ways of reading the host CSR, each forced (this rank's time)
         for mode in ("copied", "direct"):
             plan.set_host_read(mode)
-            modes[mode + "_ms"] = _time_calls(e2e_step, e2e_steps, stream)
+            modes[mode + "_ms"] = _time_each(e2e_step, e2e_steps, stream)[0]
         plan.set_host_read("auto")
         h2d = int(rp_h.numel() * 4 + ci_h.numel() * 4 + v_h.numel() * 4)
         rec["e2e"] = {"value": world * nnz / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                      "d2h_bytes_per_step": int(m * d * 4), "ms_per_step": e2e_ms, "call": "cg_apply_csr_host",
+                      "d2h_bytes_per_step": int(m * d * 4), "ms_per_step": e2e_ms, "mean_ms": e2e_mean,
+                      "calls": e2e_steps, "statistic": "median of per-call times", "call": "cg_apply_csr_host",
                       "host_read": "auto", **modes}
     del rp, ci, v, rp_h, ci_h, v_h, plan
     torch.cuda.empty_cache()

@@ -44,6 +44,37 @@ __device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p, uint64_t pol) {
     return v;
 }
 
+// Reductions into SX carry an evict-last L2 priority: each pass reduces into a part of SX
+// that fits the L2 while hundreds of MB of CSR and records stream past it (evict-first),
+// and without the hint the L2 still wrote the reduced lines back to DRAM several times
+// over (at the 2^26 x 128 ladder shape pass 1 wrote 845 MB per launch, 464 MB with the
+// hint; the replay 307 MB, 1 MB with it; sketch 0.774 -> 0.708 ms).
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void red_add_last(float *a, float v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+
+// The same reduction, or nothing where p is false (a predicated instruction, no branch).
+__device__ __forceinline__ void red_add_last_if(bool p, float *a, float v, uint64_t pol) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.global.add.L2::cache_hint.f32 [%0], %1, %3;\n\t}" ::"l"(a),
+        "f"(v), "r"(static_cast<int>(p)), "l"(pol)
+        : "memory");
+}
+
+// A record store with the evict-first hint, or nothing where p is false.
+__device__ __forceinline__ void st_stream_u2_if(bool p, uint2 *a, uint2 v, uint64_t pol) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %4;\n\t}" ::"l"(a),
+        "r"(v.x), "r"(v.y), "r"(static_cast<int>(p)), "l"(pol)
+        : "memory");
+}
+
 // Shared-memory counter of a CTA's records: returns the old value.
 __device__ __forceinline__ int add_count(int *c, int v) { return atomicAdd(c, v); }
 __device__ __forceinline__ long long add_count(long long *c, int v) {
@@ -155,7 +186,7 @@ __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, con
                                             int end, int d, float *__restrict__ SX, uint32_t bsplit,
                                             uint2 *__restrict__ region, RP cap, RP *s_count, const int *s_rp,
                                             const uint32_t *s_h, const float *s_sg, const uint8_t *s_map,
-                                            uint64_t pol, int &bad) {
+                                            uint64_t pol, uint64_t pol_last, int &bad) {
     const int lane = threadIdx.x & 31;
     for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
         int col[kScatterUnroll];
@@ -195,7 +226,7 @@ __device__ __forceinline__ void split_chunk(const int *__restrict__ col_idx, con
                     cell[u] = hb * static_cast<uint32_t>(d) + static_cast<uint32_t>(j);
                     x[u] = s_sg[lo] * v[u];
                     if (hb < bsplit)
-                        atomicAdd(SX + cell[u], x[u]);
+                        red_add_last(SX + cell[u], x[u], pol_last);
                     else
                         dfr[u] = true;
                 } else {
@@ -265,6 +296,7 @@ split_pass_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_id
     if (threadIdx.x == 0) s_count = 0;
     __syncthreads();
     const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol_last = l2_evict_last_policy();
     int bad = 0;
     for (int first = r0 + w * ROWS; first < r1; first += kWarps * ROWS) {
         int beg, end;
@@ -275,7 +307,7 @@ split_pass_kernel(const RP *__restrict__ row_ptr, const int *__restrict__ col_id
             if (mapped) map_rows<ROWS>(s_rp[w], beg, s_map[w]);
             split_chunk<ROWS, RP>(col_idx + base, vals + base, beg, end, d, SX, bsplit, records + rec_lo,
                                   rec_hi - rec_lo, &s_count, s_rp[w], s_h[w], s_sg[w], mapped ? s_map[w] : nullptr,
-                                  pol, bad);
+                                  pol, pol_last, bad);
         }
     }
     if (bad) atomicOr(status, kStatusBounds);
@@ -313,15 +345,15 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
         : "memory");
 }
 
-// The sweep of one chunk: STAGED reads nonzero k's column and value at s_col / s_val
-// [k - kbase], else from global memory; a row is found in the row map (MAPPED) or by
-// binary search over the offsets in s_rp.  Reduction or record as in split_chunk.
-template <int ROWS, bool STAGED, bool MAPPED>
-__device__ __forceinline__ void split_sweep(const int *__restrict__ col_idx, const float *__restrict__ vals,
-                                            const int *s_col, const int *s_val, int kbase, int beg, int end, int d,
-                                            float *__restrict__ SX, uint32_t lo_cell, uint2 *__restrict__ region,
-                                            int cap, int *s_count, const uint32_t *s_hw, const uint8_t *s_map,
-                                            const int *s_rp, uint64_t pol, int &bad) {
+// The sweep of a chunk whose nonzeros are not staged: nonzero k's column and value from
+// global memory, its row from the row map (MAPPED) or by binary search over the offsets
+// in s_rp.  Reduction or record as in split_chunk.
+template <int ROWS, bool MAPPED>
+__device__ __forceinline__ void split_sweep(const int *__restrict__ col_idx, const float *__restrict__ vals, int beg,
+                                            int end, int d, float *__restrict__ SX, uint32_t lo_cell,
+                                            uint2 *__restrict__ region, int cap, int *s_count, const uint32_t *s_hw,
+                                            const uint8_t *s_map, const int *s_rp, uint64_t pol, uint64_t pol_last,
+                                            int &bad) {
     const int lane = threadIdx.x & 31;
     for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
         int col[kScatterUnroll];
@@ -332,13 +364,8 @@ __device__ __forceinline__ void split_sweep(const int *__restrict__ col_idx, con
             col[u] = -1;
             v[u] = 0.0f;
             if (k0 + u * 32 < end && k < end) {  // first test warp-uniform
-                if constexpr (STAGED) {
-                    col[u] = s_col[k - kbase];
-                    v[u] = __int_as_float(s_val[k - kbase]);
-                } else {
-                    col[u] = ld_stream_i32(col_idx + k, pol);
-                    v[u] = ld_stream_f32(vals + k, pol);
-                }
+                col[u] = ld_stream_i32(col_idx + k, pol);
+                v[u] = ld_stream_f32(vals + k, pol);
             }
         }
         bool dfr[kScatterUnroll];
@@ -366,7 +393,7 @@ __device__ __forceinline__ void split_sweep(const int *__restrict__ col_idx, con
                     cell[u] = base + static_cast<uint32_t>(j);
                     x[u] = __uint_as_float(__float_as_uint(v[u]) ^ (hw & 0x80000000u));  // sigma x, exactly
                     if (base < lo_cell)
-                        atomicAdd(SX + cell[u], x[u]);
+                        red_add_last(SX + cell[u], x[u], pol_last);
                     else
                         dfr[u] = true;
                 } else {
@@ -401,6 +428,59 @@ __device__ __forceinline__ void split_sweep(const int *__restrict__ col_idx, con
     __syncwarp();
 }
 
+// The sweep of a staged chunk: nonzero k's column and value at s_col / s_val [k - kbase],
+// its row from the row map.  Without branches: a slot past the chunk's end reads the last
+// nonzero, and the reduction and the record store are predicated instructions (with
+// branches around them the pass ran 15 % more instructions).
+__device__ __forceinline__ void split_sweep_staged(const int *s_col, const int *s_val, int kbase, int beg, int end,
+                                                   int d, float *__restrict__ SX, uint32_t lo_cell,
+                                                   uint2 *__restrict__ region, int cap, int *s_count,
+                                                   const uint32_t *s_hw, const uint8_t *s_map, uint64_t pol,
+                                                   uint64_t pol_last, int &bad) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int k0 = beg; k0 < end; k0 += 32 * kScatterUnroll) {
+        bool dfr[kScatterUnroll];
+        uint32_t cell[kScatterUnroll];
+        float x[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const int k = k0 + u * 32 + lane;
+            const bool live = k < end;
+            const int kk = live ? k : end - 1;  // end > k0 >= beg
+            const int j = s_col[kk - kbase];
+            const float v = __int_as_float(s_val[kk - kbase]);
+            const uint32_t hw = s_hw[s_map[kk - beg]];
+            const bool ok = static_cast<unsigned>(j) < static_cast<unsigned>(d);
+            bad |= (live && !ok) ? 1 : 0;
+            const uint32_t base = hw & 0x7fffffffu;
+            cell[u] = base + static_cast<uint32_t>(j);
+            x[u] = __uint_as_float(__float_as_uint(v) ^ (hw & 0x80000000u));  // sigma x, exactly
+            dfr[u] = live && ok && base >= lo_cell;
+            red_add_last_if(live && ok && base < lo_cell, SX + cell[u], x[u], pol_last);
+        }
+        unsigned mask[kScatterUnroll];
+        int total = 0;
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            mask[u] = __ballot_sync(0xffffffffu, dfr[u]);
+            total += __popc(mask[u]);
+        }
+        if (total == 0) continue;  // warp-uniform
+        int at0 = 0;
+        if (lane == 0) at0 = atomicAdd(s_count, total);
+        at0 = __shfl_sync(0xffffffffu, at0, 0);
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const int at = at0 + __popc(mask[u] & below);
+            st_stream_u2_if(dfr[u] && at < cap, region + at, make_uint2(cell[u], __float_as_uint(x[u])), pol);
+            bad |= (dfr[u] && at >= cap) ? 1 : 0;
+            at0 += __popc(mask[u]);
+        }
+    }
+    __syncwarp();
+}
+
 template <int ROWS>
 __global__ void __launch_bounds__(kThreads, 5)
 split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
@@ -411,7 +491,7 @@ split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict_
     static_assert(ROWS + 1 <= 2 * kStageCap && ROWS <= 256, "row offsets fit the staging area; rows fit a byte");
     __shared__ __align__(16) int s_stage[kWarps][2 * kStageCap];  // col_idx | vals, or the row offsets
     __shared__ uint32_t s_hw[kWarps][ROWS];
-    __shared__ uint8_t s_map[kWarps][kMapCap];
+    __shared__ __align__(16) uint8_t s_map[kWarps][kMapCap];
     __shared__ __align__(8) uint64_t s_bar[kWarps];
     __shared__ int s_count;
     const int w = threadIdx.x >> 5;
@@ -437,6 +517,7 @@ split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict_
     const uint64_t pol = l2_evict_first_policy();
     uint2 *region = records + rec_lo;
     const int cap = rec_hi - rec_lo;
+    const uint64_t pol_last = l2_evict_last_policy();
     uint32_t phase = 0;
     int bad = 0, late = 0;
     for (int first = r0 + w * ROWS; first < r1; first += kWarps * ROWS) {
@@ -505,10 +586,32 @@ split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict_
                 }
             }
         }
-        if (mapped) {
+        if (mapped) {  // the row map: row starts marked, then a forward max-fill over the chunk
+            const int cnt = end - beg;
+            uint32_t *map32 = reinterpret_cast<uint32_t *>(s_map[w]);
+            for (int q = lane; 4 * q < cnt; q += 32) map32[q] = 0u;
+            __syncwarp();
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                for (int k = rp[r]; k < nx[r]; ++k) s_map[w][k - beg] = static_cast<uint8_t>(r * 32 + lane);
+            for (int r = 0; r < R; ++r)  // a non-empty row's start is no other non-empty row's
+                if (rp[r] < nx[r]) s_map[w][rp[r] - beg] = static_cast<uint8_t>(r * 32 + lane);
+            __syncwarp();
+            const int span = (cnt + 31) >> 5;  // positions per lane
+            const int p0 = lane * span;
+            int run = 0;
+            for (int i = 0; i < span; ++i)
+                if (p0 + i < cnt) run = max(run, static_cast<int>(s_map[w][p0 + i]));
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {  // inclusive max-scan of the lanes' maxima
+                const int y = __shfl_up_sync(0xffffffffu, run, o);
+                if (lane >= o) run = max(run, y);
+            }
+            run = __shfl_up_sync(0xffffffffu, run, 1);
+            if (lane == 0) run = 0;
+            for (int i = 0; i < span; ++i)
+                if (p0 + i < cnt) {
+                    run = max(run, static_cast<int>(s_map[w][p0 + i]));
+                    s_map[w][p0 + i] = static_cast<uint8_t>(run);
+                }
         }
         __syncwarp();
         if (nb > 0) {
@@ -520,14 +623,14 @@ split_pass_staged_kernel(const int *__restrict__ row_ptr, const int *__restrict_
             phase ^= 1u;
         }
         if (staged)
-            split_sweep<ROWS, true, true>(col_idx, vals, s_stage[w], s_stage[w] + kStageCap, kbase, beg, end, d, SX,
-                                          lo_cell, region, cap, &s_count, s_hw[w], s_map[w], nullptr, pol, bad);
+            split_sweep_staged(s_stage[w], s_stage[w] + kStageCap, kbase, beg, end, d, SX, lo_cell, region, cap,
+                               &s_count, s_hw[w], s_map[w], pol, pol_last, bad);
         else if (mapped)
-            split_sweep<ROWS, false, true>(col_idx, vals, nullptr, nullptr, 0, beg, end, d, SX, lo_cell, region, cap,
-                                           &s_count, s_hw[w], s_map[w], nullptr, pol, bad);
+            split_sweep<ROWS, true>(col_idx, vals, beg, end, d, SX, lo_cell, region, cap, &s_count, s_hw[w], s_map[w],
+                                    nullptr, pol, pol_last, bad);
         else
-            split_sweep<ROWS, false, false>(col_idx, vals, nullptr, nullptr, 0, beg, end, d, SX, lo_cell, region,
-                                            cap, &s_count, s_hw[w], nullptr, s_stage[w], pol, bad);
+            split_sweep<ROWS, false>(col_idx, vals, beg, end, d, SX, lo_cell, region, cap, &s_count, s_hw[w], nullptr,
+                                     s_stage[w], pol, pol_last, bad);
     }
     if (bad) atomicOr(status, kStatusBounds);
     if (late) atomicOr(status, kStatusTimeout);
@@ -564,6 +667,7 @@ replay_records_kernel(const RP *__restrict__ row_ptr, int n, int rows_per_cta, c
     const RP cnt = min(counts[blockIdx.x], __ldg(row_ptr + r1) - start);
     if (cnt <= 0) return;
     const uint64_t pol = l2_evict_first_policy();
+    const uint64_t pol_last = l2_evict_last_policy();
     constexpr int kInFlight = 4;  // record loads in flight per thread before their reductions
     RP i = threadIdx.x;
     for (; i + (kInFlight - 1) * kThreads < cnt; i += kInFlight * kThreads) {
@@ -572,11 +676,11 @@ replay_records_kernel(const RP *__restrict__ row_ptr, int n, int rows_per_cta, c
         for (int u = 0; u < kInFlight; ++u) r[u] = ld_stream_u2(records + start + i + u * kThreads, pol);
 #pragma unroll
         for (int u = 0; u < kInFlight; ++u)
-            if (r[u].x < cells) atomicAdd(SX + r[u].x, __uint_as_float(r[u].y));
+            if (r[u].x < cells) red_add_last(SX + r[u].x, __uint_as_float(r[u].y), pol_last);
     }
     for (; i < cnt; i += kThreads) {
         const uint2 r = ld_stream_u2(records + start + i, pol);
-        if (r.x < cells) atomicAdd(SX + r.x, __uint_as_float(r.y));
+        if (r.x < cells) red_add_last(SX + r.x, __uint_as_float(r.y), pol_last);
     }
 }
 

@@ -279,6 +279,47 @@ def test_deferred_scatter_edges(rows):
     plan.check()
 
 
+def _banded_csr(n, d, seed):
+    """Rows whose lengths grow along the matrix: the first third 0-2 nonzeros, the middle
+    third 1-3, the last third 4-6, so that 256-row chunks hold under 384 nonzeros (staged
+    in shared memory), 384 to 1024 (row map, global loads) and over 1024 (binary search)."""
+    rng = np.random.default_rng(seed)
+    third = n // 3
+    lens = np.concatenate([rng.integers(0, 3, third), rng.integers(1, 4, third), rng.integers(4, 7, n - 2 * third)])
+    row_ptr = np.zeros(n + 1, np.int64)
+    row_ptr[1:] = np.cumsum(lens)
+    col_idx = np.concatenate([np.sort(rng.choice(d, k, replace=False)) for k in lens]).astype(np.int32)
+    vals = rng.standard_normal(int(row_ptr[-1])).astype(np.float32)
+    return synth.CSR(n, d, row_ptr, col_idx, vals)
+
+
+@pytest.mark.parametrize("ctas", [0, 7])
+def test_deferred_staged_pass_paths(ctas):
+    """Pass 1 of the deferred scatter stages a chunk's nonzeros in shared memory by bulk
+    copies when they fit, and reads them from global memory otherwise (row map or binary
+    search): all three kinds of chunk in one matrix, with 16-byte misaligned starts and
+    ragged tails; with 7 CTAs each warp takes many chunks in turn (the mbarrier's phases);
+    col_idx and vals that are not 16-byte aligned take the plain pass."""
+    n, d, m, B, seed = 60001, 37, 13, 3001, 23
+    X = _banded_csr(n, d, 3)
+    rp, ci, v = dev_csr(X)
+    Yo, SXo = oracle.apply_csr(seed, n, d, m, B, X.row_ptr, X.col_idx, X.vals, row_offset=4097, return_sx=True)
+    plan = cg().CountGauss(n, d, m, B, seed, scatter="deferred", scatter_rows=256, row_offset=4097, sketch_ctas=ctas)
+    SX = plan.sketch_csr(rp, ci, v).cpu().numpy()
+    Y = plan.apply_csr(rp, ci, v).cpu().numpy()
+    plan.check()
+    assert rel(SX, SXo) < 1e-6
+    assert rel(Y, Yo) < FP32_TOL
+    # the same arrays one element into larger buffers: 4-byte, not 16-byte, aligned
+    ci_buf = torch.empty(X.nnz + 1, dtype=torch.int32, device=ci.device)
+    v_buf = torch.empty(X.nnz + 1, dtype=torch.float32, device=v.device)
+    ci_buf[1:].copy_(ci)
+    v_buf[1:].copy_(v)
+    SX2 = plan.sketch_csr(rp, ci_buf[1:], v_buf[1:]).cpu().numpy()
+    plan.check()
+    assert rel(SX2, SXo) < 1e-6
+
+
 @pytest.mark.parametrize("n,d,B,kind", [(70001, 37, 3001, "ragged"),      # one tile per lane row, ragged ends
                                          (300_000, 128, 4096, "bern0.01"),  # the ladder's density, 16 slices
                                          (40_000, 64, 100_000, "bern0.05"),  # 196 slices, 3.2 nonzeros per row
