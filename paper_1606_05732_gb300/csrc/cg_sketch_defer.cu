@@ -4,7 +4,7 @@
 // One fp32 reduction per nonzero runs at the L2's atomic rate only while the reduced
 // array stays in L2; past that (on GB300 from about 100 MB on) most reductions miss and
 // the rate falls several-fold.  So SX is split at bucket bsplit (B/2, or more so that the
-// lower part fills about 0.51 of the L2; deferred_split):
+// lower part fills about 0.62 of the L2; deferred_split):
 //   pass 1  streams the CSR once, hashes every row once, reduces the nonzeros of rows
 //           with h < bsplit into SX at once, and writes those of the other rows as
 //           8-byte records (h d + j, sigma x) into its CTA's region of a records buffer
@@ -697,21 +697,21 @@ int staged_rows(int n, int64_t nnz, int forced) {
 }
 
 // The bucket below which pass 1 reduces at once: for an SX past 60 % of the L2 (where the
-// automatic choice takes this scatter), the largest that keeps that part of SX at 0.51 of
-// the L2 (about 68 MB on GB300), and at least B/2 so that the part the records fill is no
+// automatic choice takes this scatter), the largest that keeps that part of SX at 0.62 of
+// the L2 (about 82 MB on GB300), and at least B/2 so that the part the records fill is no
 // larger; for a smaller SX (the scatter forced) B/2.  Past that point the lower part's
-// reductions leave the L2, short of it the records cost more instructions in pass 1 than
-// the direct reductions they replace.  Sketch times (memset and both passes) against the
-// split, 2^26 rows at 1.28 nonzeros per row: 2^18 x 128 (134 MB of SX) 0.45 B 0.872 ms,
-// 0.50 B 0.790, 0.52 B 0.788, 0.54 B 0.808, 0.58 B 0.843; 2^18 x 96 (101 MB) 0.56 B
-// 0.631, 0.64 B 0.614, 0.68 B 0.606, 0.72 B 0.636; 2^19 x 64 (134 MB) 0.48 B 0.799, 0.50 B
-// 0.774, 0.54 B 0.770, 0.58 B 0.800.  The optimum's lower part is 67-70 MB in each.
+// reductions leave the L2, short of it the records cost more than the direct reductions
+// they replace.  Sketch times (memset and both passes) against the split, 2^26 rows at
+// 1.28 nonzeros per row, with the evict-last reductions: 2^18 x 128 (134 MB of SX) 0.46 B
+// 0.722 ms, 0.50 B 0.711, 0.54 B 0.696, 0.58 B 0.680, 0.62 B 0.681; 2^18 x 96 (101 MB)
+// 0.60 B 0.565, 0.68 B 0.541, 0.76 B 0.516, 0.84 B 0.505.  The optimum's lower part is
+// 80-85 MB in both (before the evict-last hint it was 67-70 MB: 0.50-0.52 B and 0.68 B).
 uint32_t deferred_split(uint32_t B, int d) {
     const uint32_t half = B / 2;
     const int l2 = l2_bytes();
     const double sx = static_cast<double>(B) * d * sizeof(float);
     if (l2 <= 0 || d <= 0 || sx <= 0.6 * l2) return half;
-    const uint64_t fit = static_cast<uint64_t>(0.51 * l2) / (static_cast<uint64_t>(d) * sizeof(float));
+    const uint64_t fit = static_cast<uint64_t>(0.62 * l2) / (static_cast<uint64_t>(d) * sizeof(float));
     return static_cast<uint32_t>(std::min<uint64_t>(B, std::max<uint64_t>(half, fit)));
 }
 
