@@ -14,8 +14,9 @@
  *
  * Randomness.  h, sigma, G and G~ are pure functions of (seed, index): Philox4x32-10
  * (Salmon et al., SC'11) with key (lo32(seed), hi32(seed)) and counter
- * (lo32(idx), hi32(idx), tag, 0).  tag 0, idx = global row i: h(i) = floor(w0.B/2^32),
- * sigma(i) = -1 iff bit 31 of w1 is set.  Uniforms u(w) = (2(w>>9)+1).2^-24.  Entry
+ * (lo32(idx), hi32(idx), tag, 0).  tag 0, idx = floor(i/4) for global row i, w = word
+ * i mod 4 of that call: h(i) = floor(w.B/2^32), sigma(i) = -1 iff bit 0 of w is set (one
+ * call serves four consecutive rows).  Uniforms u(w) = (2(w>>9)+1).2^-24.  Entry
  * (r, c) of an R x C Gaussian with tag t is lane r%4 of the Box-Muller quadruple
  *   (sqrt(-2 ln u0) cos 2pi u1, sqrt(-2 ln u0) sin 2pi u1,
  *    sqrt(-2 ln u2) cos 2pi u3, sqrt(-2 ln u2) sin 2pi u3)
@@ -106,9 +107,11 @@ typedef enum cg_option {
                                  when SX is larger than 60 % of the L2, else 1),
                                  1 = one L2 reduction per nonzero, 2 = partition the nonzeros by
                                  bucket range and accumulate each range in shared memory, 3 =
-                                 reduce the rows of buckets below B/2 at once and write the
-                                 others as records reduced by a second pass (each half of SX in
-                                 L2 in turn; workspace + 8 bytes per nonzero; needs B d < 2^32),
+                                 reduce the rows of buckets below a split point at once and
+                                 write the others as records reduced by a second pass (each
+                                 part of SX in L2 in turn: the lower part up to 0.62 of the L2,
+                                 at least B/2; workspace + 8 bytes per nonzero; needs
+                                 B d < 2^32),
                                  4 = bin the nonzeros by slices of buckets (a power of two,
                                  at most 32768 / d) into 6-byte records and sum each slice in
                                  shared memory (workspace about 14 bytes per nonzero; needs
